@@ -1,0 +1,138 @@
+"""Seeded synthetic market-split instances.
+
+This module is the one piece shared by the CUDA path, the CPU oracle and the
+benchmark.  It only draws random numbers and packs them; it holds none of the
+method's arithmetic (no lattice, no reduction, no enumeration).
+
+Instances follow the shape of the QOBLIB market-split classes described in
+Sec. 1 of the paper: n = 10(m-1) columns, entries a_ij uniform in [0, D),
+D in {50, 100, 200}.  QOBLIB guarantees feasibility without saying how
+(Sec. 1); here every instance is made feasible by planting a binary x and
+setting d = A x.  The QOBLIB files themselves are not available, so these
+seeded instances stand in for them.
+
+Every generator uses ``numpy.random.default_rng(seed)`` (PCG64), so the
+same seed gives the same instance on every machine.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+
+@dataclass
+class Instance:
+    """One fMSP instance A x = d, x in {0,1}^n (Sec. 1, feasibility form)."""
+
+    A: np.ndarray            # int32, shape (m, n), row-major
+    d: np.ndarray            # int64, shape (m,)
+    planted: np.ndarray      # uint8, shape (n,), one known solution
+    seed: int
+    D: int
+    tag: str = ""
+
+    @property
+    def m(self) -> int:
+        return int(self.A.shape[0])
+
+    @property
+    def n(self) -> int:
+        return int(self.A.shape[1])
+
+
+def _planted(rng: np.random.Generator, n: int, ones: Optional[int]) -> np.ndarray:
+    if ones is None:
+        return rng.integers(0, 2, size=n).astype(np.uint8)
+    x = np.zeros(n, dtype=np.uint8)
+    x[rng.permutation(n)[:ones]] = 1
+    return x
+
+
+def make_instance(seed: int, m: int, n: int, D: int, ones: Optional[int] = None,
+                  tag: str = "") -> Instance:
+    """A uniform in [0, D), a planted binary x (Bernoulli(1/2), or exactly
+    ``ones`` ones at random positions), and d = A x."""
+    rng = np.random.default_rng(seed)
+    A = rng.integers(0, D, size=(m, n)).astype(np.int32)
+    x = _planted(rng, n, ones)
+    d = (A.astype(np.int64) @ x.astype(np.int64)).astype(np.int64)
+    return Instance(A=A, d=d, planted=x, seed=seed, D=D, tag=tag)
+
+
+# --- the five workloads -----------------------------------------------------
+
+def single_m3() -> List[Instance]:
+    """One instance m=3, n=20, D=100 (seed 1001)."""
+    return [make_instance(1001, 3, 20, 100, tag="m3n20")]
+
+
+def batch_m4_7(count: int = 64, first_seed: int = 2000) -> List[Instance]:
+    """``count`` instances, m drawn uniformly from {4,5,6,7} by each seed's
+    generator, n = 10(m-1), D cycling over {50, 100, 200}."""
+    out = []
+    for i in range(count):
+        seed = first_seed + i
+        rng = np.random.default_rng(seed)
+        m = int(rng.integers(4, 8))
+        n = 10 * (m - 1)
+        D = (50, 100, 200)[i % 3]
+        A = rng.integers(0, D, size=(m, n)).astype(np.int32)
+        x = rng.integers(0, 2, size=n).astype(np.uint8)
+        d = (A.astype(np.int64) @ x.astype(np.int64)).astype(np.int64)
+        out.append(Instance(A=A, d=d, planted=x, seed=seed, D=D, tag=f"batch{i}"))
+    return out
+
+
+def m8_n70(count: int = 16) -> List[Instance]:
+    """m=8, n=70, D=200, seeds 3000.. (planted Bernoulli(1/2))."""
+    return [make_instance(3000 + i, 8, 70, 200, tag=f"m8n70_{i}") for i in range(count)]
+
+
+def m9_n80(count: int = 8) -> List[Instance]:
+    """m=9, n=80, D=100, seeds 4000..; the planted x has exactly 40 ones."""
+    return [make_instance(4000 + i, 9, 80, 100, ones=40, tag=f"m9n80_{i}") for i in range(count)]
+
+
+def m12_n110(count: int = 4) -> List[Instance]:
+    """m=12, n=110, D=100, seeds 5000.. (planted Bernoulli(1/2))."""
+    return [make_instance(5000 + i, 12, 110, 100, tag=f"m12n110_{i}") for i in range(count)]
+
+
+def training_set(count: int = 256, first_seed: int = 30000) -> List[Instance]:
+    """Training instances for the subtree scorer: m cycling 5,6,7, D cycling
+    over {50, 100, 200}; seeds disjoint from every evaluation set."""
+    out = []
+    for i in range(count):
+        m = 5 + (i % 3)
+        D = (50, 100, 200)[(i // 3) % 3]
+        out.append(make_instance(first_seed + i, m, 10 * (m - 1), D, tag=f"train{i}"))
+    return out
+
+
+def small(seed: int, m: int, n: int, D: int) -> Instance:
+    """Small instances for brute-force checks (n <= 24)."""
+    return make_instance(seed, m, n, D, tag=f"small_m{m}n{n}D{D}")
+
+
+# --- packing for the batched C-ABI -------------------------------------------
+
+@dataclass
+class Packed:
+    """Concatenated instances: dims[i] = (m_i, n_i); A and d back to back."""
+
+    dims: np.ndarray                 # int32 (count, 2)
+    A: np.ndarray                    # int32 (sum m_i n_i,)
+    d: np.ndarray                    # int64 (sum m_i,)
+    instances: List[Instance] = field(default_factory=list)
+
+
+def pack(instances: List[Instance]) -> Packed:
+    dims = np.array([[x.m, x.n] for x in instances], dtype=np.int32).reshape(-1, 2)
+    A = np.concatenate([x.A.reshape(-1) for x in instances]).astype(np.int32) if instances \
+        else np.zeros(0, np.int32)
+    d = np.concatenate([x.d.reshape(-1) for x in instances]).astype(np.int64) if instances \
+        else np.zeros(0, np.int64)
+    return Packed(dims=np.ascontiguousarray(dims), A=np.ascontiguousarray(A),
+                  d=np.ascontiguousarray(d), instances=list(instances))
