@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 market-split lattice solver.
+
+One step = the whole hot path over one batch: lattice of Eq. (2), LLL,
+kernel extraction and Gram-Schmidt, top-level split and exhaustive
+enumeration of all solutions (Algorithm 1) for 64 synthetic instances with m
+uniform in {4,5,6,7}, n = 10(m-1), D cycling over {50, 100, 200} (the batch
+workload).  The metric is evaluated nodes per second (a node = one candidate
+(t, u_t) whose norm is computed).
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  `value` is device-timed with inputs resident
+in HBM; `e2e` is the same metric through the C ABI from host buffers, with
+the host->device copy of the instances and the device->host read of the
+statistics and solutions inside the timed region.  L2 is flushed between
+timed steps.  The reference arm is the CPU oracle (oracle/), timed on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "enum nodes/s; time to all sols (m=9) & first sol (m=12), learned vs plain order"
+UNIT = "nodes/s"
+WORKLOAD = "batch of 64 fMSP instances, m~U{4..7}, n=10(m-1), D in {50,100,200}, all solutions"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--lanes", type=int, default=None)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------
+def dist_init(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), hw=f[5], hwt=f[6], swt=f[7], pcap=f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+def oracle_nodes_per_s(instances, seconds: float):
+    """The CPU oracle as it stands, one thread, on instances taken in order
+    until `seconds` of work; returns (nodes/s, nodes, seconds, count)."""
+    from oracle import oracle as O
+    nodes = 0
+    t0 = time.perf_counter()
+    done = 0
+    for inst in instances:
+        r = O.solve(inst.A, inst.d).result
+        nodes += r.nodes
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return nodes / dt, nodes, dt, done
+
+
+def cpu_sample(instances):
+    """Bounded sample of the batch for the oracle: the instances with m <= 6
+    (the m = 7 instances take the oracle 3 to 70 s each)."""
+    return [x for x in instances if x.m <= 6]
+
+
+def reference_arm(args, rank, world):
+    from paper_2508_08702_gb300 import instances as I
+    if rank != 0:
+        return
+    insts = cpu_sample(I.batch_m4_7(64))
+    for _ in range(args.warmup):
+        oracle_nodes_per_s(insts[:4], 1e9)
+    vals, nodes_tot, t_tot = [], 0, 0.0
+    for _ in range(args.steps):
+        v, nodes, dt, _ = oracle_nodes_per_s(insts, 1e9)
+        vals.append(v)
+        nodes_tot += nodes
+        t_tot += dt
+    value = nodes_tot / t_tot
+    sample = f"{len(insts)} of the 64 batch instances (those with m<=6), LLL + enumeration, one thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# --------------------------------------------------------------------------
+def algorithmic_fp64_ops(stats, dims, lanes):
+    """FP64 lane operations the canonical arithmetic needs inside the
+    enumeration kernel: 3 per evaluated node (x, x^2, rho), 2 dim + log2 G + 1
+    per node passing the norm test above level 0 (w update, |w|_1 partial
+    sums and tree, slack add), plus the centre-fold fmas."""
+    ops = 0
+    for s, (m, n) in zip(stats, dims):
+        dim = n + 1
+        nodes = s["nodes"] - s["split_nodes"]
+        inner = s["passed"] - s["split_passed"] - s["leaves"]
+        ops += 3 * nodes + (2 * dim + int(math.log2(lanes)) + 1) * inner + s["center_fma"]
+    return ops
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args.gpus)
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    from paper_2508_08702_gb300 import build as B
+    from paper_2508_08702_gb300 import instances as I
+    from paper_2508_08702_gb300 import msp as M
+
+    B.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    # weak scaling: every rank runs its own batch of 64 (seeds shifted by rank)
+    insts = I.batch_m4_7(64, first_seed=2000 + 64 * rank)
+    pk = I.pack(insts)
+    kw = {} if args.lanes is None else {"lanes": args.lanes}
+    ctx = M.Context(**kw)
+    lanes = ctx.opts.lanes
+    A_dev = torch.from_numpy(pk.A).to(dev)
+    d_dev = torch.from_numpy(pk.d).to(dev)
+    A_pin = torch.from_numpy(pk.A).pin_memory()
+    d_pin = torch.from_numpy(pk.d).pin_memory()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)   # 512 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step_device():
+        ctx.msp_build_lattice(pk.dims, A_dev, d_dev)
+        ctx.msp_run_async()
+
+    for _ in range(args.warmup):
+        step_device()
+        ctx.msp_wait()
+    peak_dfma = ctx.msp_fp64_peak()
+
+    # ---- device-timed steps, inputs resident in HBM ----
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = ctx.kernel_launches
+    times, nodes_all, enum_ms, ops_all, last = [], 0, [], 0, None
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step_device()
+        e1.record(stream)
+        res = ctx.msp_wait()
+        times.append(e0.elapsed_time(e1))
+        nodes_all += res.total["nodes"]
+        ph = ctx.msp_phase_ms()
+        enum_ms.append(ph["enumerate"])
+        ops_all += algorithmic_fp64_ops(res.stats, pk.dims, lanes)
+        last = (res, ph)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    launches = ctx.kernel_launches - launches0
+    t_step = sum(times) / len(times)
+    t_max = max_over_ranks(sum(times), world)
+    nodes_sum = sum_over_ranks(nodes_all, world)
+    value = nodes_sum / (t_max / 1e3)
+
+    # ---- end to end through the C ABI from host buffers ----
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_t, h2d, d2h = [], 0, 0
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.msp_build_lattice(pk.dims, A_pin.numpy(), d_pin.numpy())
+        ctx.msp_run_async()
+        res_h = ctx.msp_wait()
+        sols = [ctx.msp_solutions(i) for i in range(len(insts))]
+        e2e_t.append(time.perf_counter() - t0)
+        h2d = pk.A.nbytes + pk.d.nbytes
+        d2h = sum(s.nbytes for s in sols) + len(insts) * 8 * 16
+    e2e_s = max_over_ranks(sum(e2e_t), world)
+    e2e_value = sum_over_ranks(res_h.total["nodes"] * len(e2e_t), world) / e2e_s
+
+    # ---- roofline of the dominant kernel (the enumerator) ----
+    res, ph = last
+    ops = algorithmic_fp64_ops(res.stats, pk.dims, lanes)
+    achieved = ops / (ph["enumerate"] / 1e3)
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_dfma / 1e9,
+            "unit": "Gop/s (FP64 lane ops)", "frac": achieved / peak_dfma, "traffic": None,
+            "peak_source": "measured FP64 fma throughput (msp_fp64_peak) on this GPU"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances": len(insts), "lanes": lanes,
+                   "l2": "flushed between steps (512 MB write)",
+                   "nodes_per_step": res.total["nodes"], "solutions_per_step": res.total["solutions"],
+                   "phase_ms": {k: round(v, 3) for k, v in ph.items()},
+                   "wall_s_timed_region": round(wall, 3)},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, nodes, dt, cnt = oracle_nodes_per_s(cpu_sample(insts), args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {cnt} batch instances with m<=6 ({nodes} nodes, {dt:.1f} s), "
+                                          f"LLL + enumeration, one thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

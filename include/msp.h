@@ -1,0 +1,215 @@
+/*
+ * msp.h -- C ABI of the GB300 (sm_103a) market-split lattice solver.
+ *
+ * Problem (Sec. 1, feasibility form fMSP): given A in Z^{m x n} and d in Z^m,
+ * list the x in {0,1}^n with A x = d.  Method (Sec. 2, Algorithm 1): embed
+ * the instance in the lattice of Eq. (2), LLL-reduce it, keep the n-m+1
+ * reduced vectors whose first m entries vanish (a basis of ker[A | -d]),
+ * Gram-Schmidt them (Eq. (4)), and enumerate exhaustively with the norm bound
+ * (first pruning condition) and the Hoelder bound of Theorem 2, checking
+ * every leaf exactly against Theorem 1.
+ *
+ * Every computational step runs in CUDA kernels on the device; the host side
+ * of this library only validates arguments, sizes buffers and launches.
+ *
+ * Conventions for all entry points
+ *   - A context owns every device buffer it allocates and releases them in
+ *     msp_destroy().  Inputs are copied: the caller keeps its buffers.
+ *   - All device work is queued on the stream given to msp_create() (NULL =
+ *     the legacy default stream).  Functions that return results to host
+ *     memory synchronise that stream before returning.
+ *   - Functions never abort the process.  They return an msp_status; per
+ *     instance failures are reported in msp_stats.status and make the batch
+ *     call return the first nonzero per-instance status.
+ *   - Calling a function before the one it depends on returns MSP_ESTATE.
+ *   - Sizes: 1 <= m <= 32, 1 <= n <= 127 (so n + 1 <= 128 lattice
+ *     coordinates after extraction), m <= n, |a_ij| < 2^31, |d_i| < 2^40.
+ */
+#ifndef MSP_H
+#define MSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MSP_API __attribute__((visibility("default")))
+#else
+#define MSP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MSP_OK = 0,
+    MSP_EINVAL = 1,      /* bad argument (size, pointer, option)                 */
+    MSP_ENOMEM = 2,      /* device or host allocation failed                     */
+    MSP_ECUDA = 3,       /* a CUDA runtime call failed (see msp_last_error)      */
+    MSP_EOVERFLOW = 4,   /* an integer left its exact range (basis, N d, u)     */
+    MSP_ERANK = 5,       /* kept vectors do not span ker[A|-d]: N too small      */
+    MSP_ETIMEOUT = 6,    /* time cap reached; results are partial                */
+    MSP_ETRUNC = 7,      /* solution buffer too small; counts stay exact         */
+    MSP_ESTATE = 8,      /* call order violated                                  */
+    MSP_ECAP = 9,        /* LLL iteration cap reached                            */
+    MSP_EQUEUE = 10      /* work queue capacity exceeded                         */
+} msp_status;
+
+typedef enum { MSP_ALL = 0, MSP_FIRST = 1 } msp_mode;      /* all solutions / stop at one  */
+typedef enum { MSP_PLAIN = 0, MSP_LEARNED = 1 } msp_order; /* queue order of the subtrees  */
+typedef enum { MSP_HOST = 0, MSP_DEVICE = 1 } msp_memory;  /* where A and d live           */
+
+/* Options.  msp_default_opts() fills the defaults given in brackets. */
+typedef struct {
+    int64_t N;             /* [1024] scale of the A-rows of Eq. (2) (Sec. 2: 2^10)      */
+    double delta;          /* [0.99] LLL Lovasz parameter                                */
+    double eta;            /* [0.51] LLL size-reduction bound on |mu|                    */
+    int64_t lll_max_iter;  /* [2e6] LLL iteration cap (MSP_ECAP when reached)            */
+    int hoelder;           /* [0] 0: Hoelder test with the one-direction cut of Sec. 2;   */
+                           /*     1: Hoelder test skips only the failing value; 2: off    */
+    int sym;               /* [1] 1: enumerate one of v, -v (first nonzero u > 0);        */
+                           /*     0: both signs, keep leaves whose last entry is +1       */
+    int use_eps;           /* [1] slack eps = (n+1) 2^-20 on both tests (0: none)         */
+    int lanes;             /* [16] lanes per subtree walker: 8, 16 or 32.  Also fixes the */
+                           /*      summation order of ||w||_1 (G interleaved partial sums */
+                           /*      combined pairwise), so node counts depend on it        */
+    int split_depth;       /* [24] maximum number of top levels the splitter expands      */
+    int split_target;      /* [0] stop splitting once an instance has this many subtree   */
+                           /*     prefixes (0: 8 x the number of walkers / instances)     */
+    int split_capacity;    /* [0] prefixes stored per instance (0: 4 x split_target)      */
+    int warps_per_block;   /* [8] enumerator block size in warps                          */
+    int blocks_per_sm;     /* [0] enumerator blocks per SM (0: occupancy-derived)          */
+    int smem_tables;       /* [1] stage mu/bhat/B in shared memory when they fit           */
+    int64_t sol_capacity;  /* [1<<20] solutions stored (over all instances)               */
+    double max_seconds;    /* [600] safety cap on every enumeration's device time; the     */
+                           /*       walkers stop and report MSP_ETIMEOUT when it passes   */
+} msp_opts;
+
+/* Per-instance results of an enumeration. */
+typedef struct {
+    int64_t nodes;         /* evaluated nodes: one per candidate (t, u_t) whose norm   */
+                           /* ||w^(t)||^2 was computed (split part + subtrees)          */
+    int64_t passed;        /* nodes that passed the norm test                          */
+    int64_t leaves;        /* passed nodes at level 0 (exact Theorem 1 check)          */
+    int64_t solutions;     /* x with A x = d found (exact count even if truncated)     */
+    int64_t prefixes;      /* subtrees created by the splitter                         */
+    int32_t split_level;   /* lowest level fixed by the splitter                       */
+    int32_t kernel_rank;   /* number of kept vectors d = n - rank + 1                   */
+    int64_t lll_iterations;
+    int64_t lll_swaps;
+    int64_t split_nodes;   /* part of `nodes` evaluated by the splitter               */
+    int64_t split_passed;  /* part of `passed` evaluated by the splitter              */
+    int64_t center_fma;    /* fmas spent by the walkers on the centres y_t            */
+    int32_t status;        /* msp_status of this instance                              */
+    int32_t reserved;
+    double ms;             /* wall time of the enumeration call (whole batch)          */
+} msp_stats;
+
+typedef struct msp_ctx msp_ctx;
+
+/* Fill *opts with the defaults listed above. */
+MSP_API void msp_default_opts(msp_opts *opts);
+
+/* Create a context on the current CUDA device.  opts may be NULL (defaults);
+ * stream is a cudaStream_t (NULL: default stream).  *out receives the
+ * context or NULL on failure. */
+MSP_API msp_status msp_create(msp_ctx **out, const msp_opts *opts, void *stream);
+
+/* Release every device buffer of the context and the context itself.
+ * Synchronises the context's stream first.  NULL is ignored. */
+MSP_API void msp_destroy(msp_ctx *ctx);
+
+/* Step a1 -- lattice of Eq. (2) (Sec. 2), binary bounds (r_max = c_j = 1),
+ * for a batch of `count` instances.
+ *   dims  host int32[count][2] = (m_i, n_i)
+ *   A     int32, the A_i row-major (m_i x n_i) back to back
+ *   d     int64, the d_i back to back
+ *   mem   MSP_HOST: A, d are host pointers (copied host->device on the
+ *         stream); MSP_DEVICE: device pointers, read before the next
+ *         synchronising call returns.
+ * Allocates (or reuses) the batch's device buffers, then builds each
+ * instance's (m+n+1) x (n+1) generator on the device.  Any later call
+ * works on this batch until the next msp_build_lattice(). */
+MSP_API msp_status msp_build_lattice(msp_ctx *ctx, int count, const int32_t *dims,
+                             const int32_t *A, const int64_t *d, int mem);
+
+/* Steps a2-a3 -- Alg. 1 steps 1-3: LLL-reduce every generator (exact
+ * integer basis, exact int64 Gram matrix, FP64 Gram-Schmidt), keep the
+ * reduced vectors whose first m entries are zero, drop those rows and
+ * compute the FP64 Gram-Schmidt tables mu, ||bhat||^2, bhat (Eq. (4)).
+ * Asynchronous; per-instance errors (MSP_EOVERFLOW, MSP_ERANK, MSP_ECAP)
+ * surface in msp_enumerate's statistics. */
+MSP_API msp_status msp_reduce(msp_ctx *ctx);
+
+/* Steps a4-a7 -- Algorithm 1: split the top levels into subtree prefixes,
+ * optionally reorder them by the learned scorer (MSP_LEARNED; falls back
+ * to MSP_PLAIN when no scorer is loaded), enumerate every subtree on the
+ * device and check every leaf exactly (Theorem 1).  MSP_FIRST stops all
+ * walkers once one solution is verified.  time_cap_s > 0 bounds the
+ * enumeration's wall time (MSP_ETIMEOUT, partial results).
+ * stats: NULL or count entries (one per instance).  total: NULL or one
+ * entry summed over the batch.  Synchronises the stream. */
+MSP_API msp_status msp_enumerate(msp_ctx *ctx, int mode, int order, double time_cap_s,
+                         msp_stats *stats, msp_stats *total);
+
+/* Asynchronous variant: queue a whole step (reduce + split + enumerate +
+ * collect) for the current batch without synchronising, so that it can be
+ * timed with events or captured in a CUDA graph.  Read the results with
+ * msp_wait(). */
+MSP_API msp_status msp_run_async(msp_ctx *ctx, int mode, int order);
+
+/* Synchronise and read the statistics of the last msp_run_async(). */
+MSP_API msp_status msp_wait(msp_ctx *ctx, msp_stats *stats, msp_stats *total);
+
+/* Solutions of instance `inst` after msp_enumerate / msp_wait: writes up to
+ * cap rows of n bytes (0/1), lexicographically sorted, into host memory x,
+ * and the full count into *count.  cap = 0 (x may be NULL) only queries the
+ * count.  Returns MSP_ETRUNC when the count exceeds cap or the context's
+ * solution capacity. */
+MSP_API msp_status msp_solutions(msp_ctx *ctx, int inst, uint8_t *x, size_t cap, size_t *count);
+
+/* Export instance `inst`'s reduced kernel basis and Gram-Schmidt tables to
+ * host memory (for inspection and tests).  dims_out[0] = kernel rank dd,
+ * dims_out[1] = n + 1.  Any pointer may be NULL to skip it; otherwise
+ * basis holds dd*(n+1) int32, mu dd*dd doubles (mu[i][j], row-major, 1 on
+ * the diagonal), B dd doubles, bhat dd*(n+1) doubles. */
+MSP_API msp_status msp_export_gso(msp_ctx *ctx, int inst, int32_t *dims_out, int32_t *basis,
+                          double *mu, double *B, double *bhat);
+
+/* Export instance `inst`'s full LLL-reduced basis: (n+1) x (m+n+1) int64,
+ * one reduced vector per row, into host memory. */
+MSP_API msp_status msp_export_reduced(msp_ctx *ctx, int inst, int64_t *basis);
+
+/* Export the subtree prefixes of instance `inst` made by the last split
+ * (the tree partition of Sec. 4), in depth-first order: up to cap rows of
+ * dd int32 u values (entries below the split level are 0), their partial
+ * norms rho, and the log of the last enumeration -- nodes evaluated in each
+ * subtree (negative if the walk was cut short) and solutions found in it.
+ * *count receives the number of prefixes and *split_level the lowest fixed
+ * level.  Any array may be NULL. */
+MSP_API msp_status msp_export_prefixes(msp_ctx *ctx, int inst, int32_t *u, double *rho, int64_t *nodes,
+                                       int32_t *sols, size_t cap, size_t *count, int32_t *split_level);
+
+/* Device time in milliseconds of the phases of the last enumeration,
+ * measured with CUDA events on the context's stream: out[0] reduction
+ * (LLL + Gram-Schmidt, if msp_reduce or msp_run_async queued it), out[1]
+ * split, out[2] enumeration kernel, out[3] solution collection. */
+MSP_API msp_status msp_phase_ms(msp_ctx *ctx, double *out);
+
+/* Measure this GPU's FP64 fused multiply-add throughput: a kernel of
+ * independent FMA chains on every SM, timed with CUDA events on the
+ * context's stream.  *dfma_per_s receives FMA instructions (lanes) per
+ * second.  Used as the measured peak of the enumeration roofline. */
+MSP_API msp_status msp_fp64_peak(msp_ctx *ctx, double *dfma_per_s);
+
+/* Human-readable name of a status code, and the context's last error text. */
+MSP_API const char *msp_status_string(int status);
+MSP_API const char *msp_last_error(const msp_ctx *ctx);
+
+/* Number of CUDA kernels launched by this context since creation. */
+MSP_API int64_t msp_kernel_launches(const msp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSP_H */

@@ -1,0 +1,588 @@
+// api.cu -- C ABI of include/msp.h: argument checks, device buffers, launches.
+// Every computational step is a kernel in lattice.cu / enum.cu; this file
+// only sizes buffers, queues work on the context's stream and copies
+// results back.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/msp.h"
+#include "common.cuh"
+
+namespace msp {
+__global__ void build_lattice_kernel(Pools P, int64_t N);
+__global__ void lll_kernel(Pools P, double delta, double eta, int64_t max_iter, unsigned long long max_ns);
+__global__ void extract_gso_kernel(Pools P);
+cudaError_t launch_split(const Pools& P, const EnumCfg& cfg, int lanes, int max_depth, int64_t target,
+                         int64_t* fcnt, cudaStream_t st);
+cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
+                        int Kmax, int dimPad, cudaStream_t st);
+cudaError_t launch_collect(const Pools& P, int64_t* soff, unsigned long long* fill, SolRec* seg, SolRec* out,
+                           cudaStream_t st);
+cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, cudaStream_t st);
+int64_t walker_bytes(int Kmax, int dimPad);
+int enum_blocks_per_sm(int lanes, int threads);
+cudaError_t fp64_peak(double* dfma_per_s, int sms, cudaStream_t st);
+}  // namespace msp
+
+using namespace msp;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct msp_ctx {
+    msp_opts o;
+    cudaStream_t st = nullptr;
+    int dev = 0, sms = 0;
+    std::string err;
+    int64_t launches = 0;
+    int state = 0;   // 0 empty, 1 lattice built, 2 reduced, 3 enumerated
+    // batch
+    int count = 0, Kmax = 0, dimMax = 0, dimPad = 0;
+    int64_t F = 0;
+    std::vector<InstDesc> hinst;
+    std::vector<msp_stats> stats;
+    int last_mode = 0;
+    double last_ms = 0.0;
+    std::chrono::steady_clock::time_point t_start;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t evr0 = nullptr, evr1 = nullptr;   // reduce
+    cudaEvent_t evs1 = nullptr, eve1 = nullptr;   // split end, enumerate end
+    bool reduce_timed = false;
+    // device buffers
+    Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, fu, frho, fw, fcnt, qbase, sols, ctrl, soff,
+        fill, seg, sout, scratch, plog_nodes, plog_sols;
+    std::vector<int64_t> soff_h;
+    std::vector<SolRec> sout_h;
+    bool sout_valid = false;
+    Pools P{};
+};
+
+namespace {
+
+msp_status fail(msp_ctx* c, msp_status s, const std::string& what) {
+    if (c) c->err = what;
+    return s;
+}
+
+msp_status cuda_fail(msp_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, MSP_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+msp_status ensure(msp_ctx* c, Buf& b, size_t bytes, const char* name) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return MSP_OK;
+    if (b.p) {
+        cudaStreamSynchronize(c->st);
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, MSP_ENOMEM, std::string("cudaMalloc ") + name + " (" + std::to_string(bytes) + " bytes): " +
+                                       cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return MSP_OK;
+}
+
+template <class T>
+T* ptr(Buf& b) {
+    return static_cast<T*>(b.p);
+}
+
+void refresh_pools(msp_ctx* c) {
+    Pools& P = c->P;
+    P.inst = ptr<InstDesc>(c->inst);
+    P.cnt = ptr<InstCounters>(c->cnt);
+    P.count = c->count;
+    P.Kmax = c->Kmax;
+    P.dimMax = c->dimMax;
+    P.dimPad = c->dimPad;
+    P.A = ptr<int32_t>(c->A);
+    P.d = ptr<int64_t>(c->d);
+    P.basis = ptr<int64_t>(c->basis);
+    P.gram = ptr<int64_t>(c->gram);
+    P.mu = ptr<double>(c->mu);
+    P.Bl = ptr<double>(c->Bl);
+    P.kb = ptr<int32_t>(c->kb);
+    P.muT = ptr<double>(c->muT);
+    P.B = ptr<double>(c->B);
+    P.bhat = ptr<double>(c->bhat);
+    P.fu = ptr<int32_t>(c->fu);
+    P.frho = ptr<double>(c->frho);
+    P.fw = ptr<double>(c->fw);
+    P.F = c->F;
+    P.qbase = ptr<int64_t>(c->qbase);
+    P.qperm = nullptr;
+    P.plog_nodes = ptr<int64_t>(c->plog_nodes);
+    P.plog_sols = ptr<int32_t>(c->plog_sols);
+    P.sols = ptr<SolRec>(c->sols);
+    P.sol_cap = c->o.sol_capacity;
+    P.ctrl = ptr<Ctrl>(c->ctrl);
+}
+
+int walkers_of(const msp_ctx* c, int blocks, int threads) { return blocks * threads / c->o.lanes; }
+
+void enum_launch_shape(const msp_ctx* c, int* blocks, int* threads) {
+    *threads = c->o.warps_per_block * 32;
+    int bps = c->o.blocks_per_sm;
+    if (bps <= 0) bps = std::max(1, enum_blocks_per_sm(c->o.lanes, *threads));
+    *blocks = c->sms * bps;
+}
+
+msp_status check_launch(msp_ctx* c, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return MSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void msp_default_opts(msp_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->N = 1024;
+    o->delta = 0.99;
+    o->eta = 0.51;
+    o->lll_max_iter = 2000000;
+    o->hoelder = 0;
+    o->sym = 1;
+    o->use_eps = 1;
+    o->lanes = 16;
+    o->split_depth = 24;
+    o->split_target = 0;
+    o->split_capacity = 0;
+    o->warps_per_block = 8;
+    o->blocks_per_sm = 0;
+    o->smem_tables = 1;
+    o->sol_capacity = 1 << 20;
+    o->max_seconds = 600.0;
+}
+
+const char* msp_status_string(int s) {
+    switch (s) {
+        case MSP_OK: return "ok";
+        case MSP_EINVAL: return "invalid argument";
+        case MSP_ENOMEM: return "out of memory";
+        case MSP_ECUDA: return "CUDA error";
+        case MSP_EOVERFLOW: return "integer overflow";
+        case MSP_ERANK: return "kept vectors do not span the kernel (N too small)";
+        case MSP_ETIMEOUT: return "time cap reached";
+        case MSP_ETRUNC: return "solution buffer too small";
+        case MSP_ESTATE: return "call order violated";
+        case MSP_ECAP: return "LLL iteration cap reached";
+        case MSP_EQUEUE: return "work queue capacity exceeded";
+        default: return "unknown status";
+    }
+}
+
+const char* msp_last_error(const msp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t msp_kernel_launches(const msp_ctx* c) { return c ? c->launches : 0; }
+
+msp_status msp_create(msp_ctx** out, const msp_opts* opts, void* stream) {
+    if (!out) return MSP_EINVAL;
+    *out = nullptr;
+    msp_ctx* c = new (std::nothrow) msp_ctx();
+    if (!c) return MSP_ENOMEM;
+    if (opts) c->o = *opts; else msp_default_opts(&c->o);
+    const msp_opts& o = c->o;
+    if (o.N < 1 || o.N > (1LL << 30) || !(o.delta > 0.25 && o.delta < 1.0) || !(o.eta >= 0.5 && o.eta < 1.0) ||
+        o.hoelder < 0 || o.hoelder > 2 || (o.lanes != 8 && o.lanes != 16 && o.lanes != 32) ||
+        o.split_depth < 0 || o.warps_per_block < 1 || o.warps_per_block > 8 || o.sol_capacity < 1 ||
+        o.lll_max_iter < 1 || !(o.max_seconds > 0.0)) {
+        delete c;
+        return MSP_EINVAL;
+    }
+    c->st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&c->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->evr0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->evr1);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->evs1);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->eve1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return MSP_ECUDA;
+    }
+    *out = c;
+    return MSP_OK;
+}
+
+void msp_destroy(msp_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    Buf* all[] = {&c->inst, &c->cnt, &c->A, &c->d, &c->basis, &c->gram, &c->mu, &c->Bl, &c->kb, &c->muT, &c->B,
+                  &c->bhat, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
+                  &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols};
+    for (Buf* b : all)
+        if (b->p) cudaFree(b->p);
+    for (cudaEvent_t ev : {c->ev0, c->ev1, c->evr0, c->evr1, c->evs1, c->eve1})
+        if (ev) cudaEventDestroy(ev);
+    delete c;
+}
+
+msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const int32_t* A, const int64_t* d,
+                             int mem) {
+    if (!c) return MSP_EINVAL;
+    if (count < 1 || !dims || !A || !d || (mem != MSP_HOST && mem != MSP_DEVICE))
+        return fail(c, MSP_EINVAL, "msp_build_lattice: bad arguments");
+    std::vector<InstDesc> h(count);
+    int64_t nA = 0, nd = 0, nBasis = 0, nGram = 0, nMu = 0, nK = 0, nKb = 0, nT = 0;
+    int Kmax = 0, dimMax = 0;
+    for (int i = 0; i < count; ++i) {
+        const int m = dims[2 * i], n = dims[2 * i + 1];
+        if (m < 1 || m > kMaxM || n < 1 || n + 1 > kMaxDim || m > n)
+            return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(i) + " has bad (m, n)");
+        InstDesc& I = h[i];
+        std::memset(&I, 0, sizeof I);
+        I.m = m; I.n = n; I.K = n + 1; I.L = m + n + 1; I.dim = n + 1;
+        I.offA = nA; nA += (int64_t)m * n;
+        I.offd = nd; nd += m;
+        I.offBasis = nBasis; nBasis += (int64_t)I.K * I.L;
+        I.offGram = nGram; nGram += (int64_t)I.K * I.K;
+        I.offMu = nMu; nMu += (int64_t)2 * I.K * I.K;
+        I.offBl = nK; I.offB = nK; nK += I.K;
+        I.offKb = nKb; I.offBhat = nKb; nKb += (int64_t)I.K * I.dim;
+        I.offMuT = nT; nT += (int64_t)I.K * I.K;
+        Kmax = std::max(Kmax, I.K);
+        dimMax = std::max(dimMax, I.dim);
+    }
+    c->count = count;
+    c->Kmax = Kmax;
+    c->dimMax = dimMax;
+    c->dimPad = (dimMax + 31) / 32 * 32;
+    // split sizes
+    int blocks, threads;
+    enum_launch_shape(c, &blocks, &threads);
+    const int64_t walkers = walkers_of(c, blocks, threads);
+    int64_t target = c->o.split_target > 0 ? c->o.split_target : std::max<int64_t>(64, 8 * walkers / count);
+    c->F = c->o.split_capacity > 0 ? std::max<int64_t>(c->o.split_capacity, 1) : 4 * target;
+    msp_status s;
+#define ENSURE(buf, bytes)                                               \
+    if ((s = ensure(c, c->buf, (size_t)(bytes), #buf)) != MSP_OK) return s;
+    ENSURE(inst, sizeof(InstDesc) * count);
+    ENSURE(cnt, sizeof(InstCounters) * count);
+    ENSURE(A, sizeof(int32_t) * nA);
+    ENSURE(d, sizeof(int64_t) * nd);
+    ENSURE(basis, sizeof(int64_t) * nBasis);
+    ENSURE(gram, sizeof(int64_t) * nGram);
+    ENSURE(mu, sizeof(double) * nMu);
+    ENSURE(Bl, sizeof(double) * nK);
+    ENSURE(kb, sizeof(int32_t) * nKb);
+    ENSURE(muT, sizeof(double) * nT);
+    ENSURE(B, sizeof(double) * nK);
+    ENSURE(bhat, sizeof(double) * nKb);
+    ENSURE(fu, sizeof(int32_t) * (size_t)count * 2 * c->F * Kmax);
+    ENSURE(frho, sizeof(double) * (size_t)count * 2 * c->F);
+    ENSURE(fw, sizeof(double) * (size_t)count * 2 * c->F * c->dimPad);
+    ENSURE(fcnt, sizeof(int64_t) * (size_t)count * c->F);
+    ENSURE(plog_nodes, sizeof(int64_t) * (size_t)count * c->F);
+    ENSURE(plog_sols, sizeof(int32_t) * (size_t)count * c->F);
+    ENSURE(qbase, sizeof(int64_t) * (count + 1));
+    ENSURE(sols, sizeof(SolRec) * (size_t)c->o.sol_capacity);
+    ENSURE(ctrl, sizeof(Ctrl));
+    ENSURE(soff, sizeof(int64_t) * (count + 1));
+    ENSURE(fill, sizeof(unsigned long long) * count);
+    ENSURE(seg, sizeof(SolRec) * (size_t)c->o.sol_capacity);
+    ENSURE(sout, sizeof(SolRec) * (size_t)c->o.sol_capacity);
+    ENSURE(scratch, (size_t)walkers * walker_bytes(Kmax, c->dimPad));
+#undef ENSURE
+    refresh_pools(c);
+    const cudaMemcpyKind kind = (mem == MSP_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaMemcpyAsync(c->A.p, A, sizeof(int32_t) * nA, kind, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d.p, d, sizeof(int64_t) * nd, kind, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->inst.p, h.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt.p, 0, sizeof(InstCounters) * count, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_build_lattice copies");
+    c->hinst = h;
+    build_lattice_kernel<<<count, 128, 0, c->st>>>(c->P, c->o.N);
+    ++c->launches;
+    if ((s = check_launch(c, "build_lattice_kernel")) != MSP_OK) return s;
+    c->state = 1;
+    c->sout_valid = false;
+    return MSP_OK;
+}
+
+msp_status msp_reduce(msp_ctx* c) {
+    if (!c) return MSP_EINVAL;
+    if (c->state < 1) return fail(c, MSP_ESTATE, "msp_reduce before msp_build_lattice");
+    cudaEventRecord(c->evr0, c->st);
+    lll_kernel<<<c->count, 32, 0, c->st>>>(c->P, c->o.delta, c->o.eta, c->o.lll_max_iter,
+                                           (unsigned long long)(c->o.max_seconds * 1e9));
+    ++c->launches;
+    msp_status s = check_launch(c, "lll_kernel");
+    if (s != MSP_OK) return s;
+    extract_gso_kernel<<<c->count, 32, 0, c->st>>>(c->P);
+    ++c->launches;
+    if ((s = check_launch(c, "extract_gso_kernel")) != MSP_OK) return s;
+    cudaEventRecord(c->evr1, c->st);
+    c->reduce_timed = true;
+    c->state = 2;
+    return MSP_OK;
+}
+
+static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_cap_s) {
+    (void)order;   // the learned order is attached by the scorer module
+    EnumCfg cfg{c->o.hoelder, c->o.sym, c->o.use_eps, mode == MSP_FIRST ? 1 : 0};
+    int blocks, threads;
+    enum_launch_shape(c, &blocks, &threads);
+    const int64_t walkers = walkers_of(c, blocks, threads);
+    msp_status s = ensure(c, c->scratch, (size_t)walkers * walker_bytes(c->Kmax, c->dimPad), "scratch");
+    if (s != MSP_OK) return s;
+    int64_t target = c->o.split_target > 0 ? c->o.split_target : std::max<int64_t>(64, 8 * walkers / c->count);
+    target = std::min<int64_t>(target, c->F);
+    cudaError_t e = cudaMemsetAsync(c->cnt.p, 0, sizeof(InstCounters) * c->count, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->plog_nodes.p, 0, c->plog_nodes.bytes, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->plog_sols.p, 0, c->plog_sols.bytes, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset counters");
+    // the caller's cap, else the context's safety cap: no walk outlives it
+    const double cap_s = time_cap_s > 0 ? std::min(time_cap_s, c->o.max_seconds) : c->o.max_seconds;
+    const unsigned long long cap_ns = (unsigned long long)(cap_s * 1e9);
+    cudaEventRecord(c->ev0, c->st);
+    if ((e = launch_start(ptr<Ctrl>(c->ctrl), cap_ns, c->st)) != cudaSuccess) return cuda_fail(c, e, "start");
+    ++c->launches;
+    if ((e = launch_split(c->P, cfg, c->o.lanes, c->o.split_depth, target, ptr<int64_t>(c->fcnt), c->st)) !=
+        cudaSuccess)
+        return cuda_fail(c, e, "split");
+    c->launches += 2;
+    cudaEventRecord(c->evs1, c->st);
+    if ((e = launch_enum(c->P, cfg, c->o.lanes, blocks, threads, ptr<char>(c->scratch), c->Kmax, c->dimPad, c->st)) !=
+        cudaSuccess)
+        return cuda_fail(c, e, "enumerate");
+    ++c->launches;
+    cudaEventRecord(c->eve1, c->st);
+    if ((e = launch_collect(c->P, ptr<int64_t>(c->soff), ptr<unsigned long long>(c->fill), ptr<SolRec>(c->seg),
+                            ptr<SolRec>(c->sout), c->st)) != cudaSuccess)
+        return cuda_fail(c, e, "collect");
+    c->launches += 4;
+    cudaEventRecord(c->ev1, c->st);
+    c->last_mode = mode;
+    c->state = 3;
+    c->sout_valid = false;
+    return MSP_OK;
+}
+
+msp_status msp_run_async(msp_ctx* c, int mode, int order) {
+    if (!c) return MSP_EINVAL;
+    if (c->state < 1) return fail(c, MSP_ESTATE, "msp_run_async before msp_build_lattice");
+    if (mode != MSP_ALL && mode != MSP_FIRST) return fail(c, MSP_EINVAL, "bad mode");
+    msp_status s = msp_reduce(c);
+    if (s != MSP_OK) return s;
+    return queue_enumerate(c, mode, order, 0.0);
+}
+
+msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {
+    if (!c) return MSP_EINVAL;
+    if (c->state < 3) return fail(c, MSP_ESTATE, "msp_wait before an enumeration");
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "enumeration");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    c->last_ms = ms;
+    std::vector<InstDesc> h(c->count);
+    std::vector<InstCounters> cn(c->count);
+    Ctrl ctl;
+    c->soff_h.assign(c->count + 1, 0);
+    e = cudaMemcpy(h.data(), c->inst.p, sizeof(InstDesc) * c->count, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(cn.data(), c->cnt.p, sizeof(InstCounters) * c->count, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&ctl, c->ctrl.p, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->soff_h.data(), c->soff.p, sizeof(int64_t) * (c->count + 1), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading results");
+    c->hinst = h;
+    c->stats.assign(c->count, msp_stats{});
+    msp_status first_bad = MSP_OK;
+    msp_stats tot{};
+    const bool trunc = (int64_t)ctl.nsol_total > c->o.sol_capacity;
+    for (int i = 0; i < c->count; ++i) {
+        msp_stats& S = c->stats[i];
+        S.nodes = (int64_t)cn[i].nodes;
+        S.passed = (int64_t)cn[i].passed;
+        S.leaves = (int64_t)cn[i].leaves;
+        S.solutions = (int64_t)cn[i].nsol;
+        S.prefixes = h[i].nprefix;
+        S.split_level = h[i].split_level;
+        S.kernel_rank = h[i].dd;
+        S.lll_iterations = h[i].lll_iters;
+        S.lll_swaps = h[i].lll_swaps;
+        S.split_nodes = (int64_t)cn[i].split_nodes;
+        S.split_passed = (int64_t)cn[i].split_passed;
+        S.center_fma = (int64_t)cn[i].center_fma;
+        int32_t st = h[i].status;
+        if (st == MSP_OK && ctl.stop == 2) st = MSP_ETIMEOUT;
+        if (st == MSP_OK && trunc) st = MSP_ETRUNC;
+        S.status = st;
+        S.ms = ms;
+        if (st != MSP_OK && first_bad == MSP_OK) first_bad = (msp_status)st;
+        tot.nodes += S.nodes;
+        tot.passed += S.passed;
+        tot.leaves += S.leaves;
+        tot.solutions += S.solutions;
+        tot.prefixes += S.prefixes;
+        tot.lll_iterations += S.lll_iterations;
+        tot.lll_swaps += S.lll_swaps;
+        tot.split_nodes += S.split_nodes;
+        tot.split_passed += S.split_passed;
+        tot.center_fma += S.center_fma;
+    }
+    tot.status = first_bad;
+    tot.ms = ms;
+    if (stats) std::memcpy(stats, c->stats.data(), sizeof(msp_stats) * c->count);
+    if (total) *total = tot;
+    return first_bad;
+}
+
+msp_status msp_enumerate(msp_ctx* c, int mode, int order, double time_cap_s, msp_stats* stats, msp_stats* total) {
+    if (!c) return MSP_EINVAL;
+    if (c->state < 2) return fail(c, MSP_ESTATE, "msp_enumerate before msp_reduce");
+    if (mode != MSP_ALL && mode != MSP_FIRST) return fail(c, MSP_EINVAL, "bad mode");
+    if (order != MSP_PLAIN && order != MSP_LEARNED) return fail(c, MSP_EINVAL, "bad order");
+    msp_status s = queue_enumerate(c, mode, order, time_cap_s);
+    if (s != MSP_OK) return s;
+    return msp_wait(c, stats, total);
+}
+
+msp_status msp_fp64_peak(msp_ctx* c, double* dfma_per_s) {
+    if (!c || !dfma_per_s) return MSP_EINVAL;
+    cudaError_t e = fp64_peak(dfma_per_s, c->sms, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_fp64_peak");
+    c->launches += 4;
+    return MSP_OK;
+}
+
+msp_status msp_phase_ms(msp_ctx* c, double* out) {
+    if (!c || !out) return MSP_EINVAL;
+    if (c->state < 3) return fail(c, MSP_ESTATE, "msp_phase_ms before an enumeration");
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_phase_ms");
+    float r = 0.f, s = 0.f, n = 0.f, k = 0.f;
+    if (c->reduce_timed) cudaEventElapsedTime(&r, c->evr0, c->evr1);
+    cudaEventElapsedTime(&s, c->ev0, c->evs1);
+    cudaEventElapsedTime(&n, c->evs1, c->eve1);
+    cudaEventElapsedTime(&k, c->eve1, c->ev1);
+    out[0] = r; out[1] = s; out[2] = n; out[3] = k;
+    return MSP_OK;
+}
+
+msp_status msp_solutions(msp_ctx* c, int inst, uint8_t* x, size_t cap, size_t* count) {
+    if (!c || !count) return MSP_EINVAL;
+    if (c->state < 3 || c->stats.empty()) return fail(c, MSP_ESTATE, "msp_solutions before msp_wait");
+    if (inst < 0 || inst >= c->count) return fail(c, MSP_EINVAL, "instance index out of range");
+    const int64_t found = c->stats[inst].solutions;
+    *count = (size_t)found;
+    if (cap == 0) return MSP_OK;
+    if (!x) return MSP_EINVAL;
+    const int64_t lo = c->soff_h[inst];
+    const int64_t have = c->soff_h[inst + 1] - lo;   // stored records of this instance
+    const int64_t take = std::min<int64_t>(have, (int64_t)cap);
+    std::vector<SolRec> rec(take);
+    if (take > 0) {
+        cudaError_t e = cudaMemcpy(rec.data(), ptr<SolRec>(c->sout) + lo, sizeof(SolRec) * take, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "msp_solutions copy");
+    }
+    const int n = c->hinst[inst].n;
+    for (int64_t k = 0; k < take; ++k)
+        for (int j = 0; j < n; ++j) {
+            const unsigned long long w = j < 64 ? rec[k].hi : rec[k].lo;
+            const int bit = j < 64 ? 63 - j : 127 - j;
+            x[(size_t)k * n + j] = (uint8_t)((w >> bit) & 1ULL);
+        }
+    return (take < found) ? MSP_ETRUNC : MSP_OK;
+}
+
+msp_status msp_export_gso(msp_ctx* c, int inst, int32_t* dims_out, int32_t* basis, double* mu, double* B,
+                          double* bhat) {
+    if (!c) return MSP_EINVAL;
+    if (c->state < 2) return fail(c, MSP_ESTATE, "msp_export_gso before msp_reduce");
+    if (inst < 0 || inst >= c->count) return fail(c, MSP_EINVAL, "instance index out of range");
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_export_gso sync");
+    InstDesc I;
+    e = cudaMemcpy(&I, ptr<InstDesc>(c->inst) + inst, sizeof I, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_export_gso");
+    if (I.status != MSP_OK) return (msp_status)I.status;
+    const int dd = I.dd, dim = I.dim;
+    if (dims_out) { dims_out[0] = dd; dims_out[1] = dim; }
+    if (basis) e = cudaMemcpy(basis, ptr<int32_t>(c->kb) + I.offKb, sizeof(int32_t) * dd * dim, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && B) e = cudaMemcpy(B, ptr<double>(c->B) + I.offB, sizeof(double) * dd, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && bhat)
+        e = cudaMemcpy(bhat, ptr<double>(c->bhat) + I.offBhat, sizeof(double) * dd * dim, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && mu) {
+        std::vector<double> t((size_t)dd * dd);
+        e = cudaMemcpy(t.data(), ptr<double>(c->muT) + I.offMuT, sizeof(double) * dd * dd, cudaMemcpyDeviceToHost);
+        for (int i = 0; i < dd; ++i)
+            for (int j = 0; j < dd; ++j) mu[(size_t)i * dd + j] = (j <= i) ? t[(size_t)j * dd + i] : 0.0;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_export_gso copies");
+    return MSP_OK;
+}
+
+msp_status msp_export_reduced(msp_ctx* c, int inst, int64_t* basis) {
+    if (!c || !basis) return MSP_EINVAL;
+    if (c->state < 2) return fail(c, MSP_ESTATE, "msp_export_reduced before msp_reduce");
+    if (inst < 0 || inst >= c->count) return fail(c, MSP_EINVAL, "instance index out of range");
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    InstDesc I;
+    if (e == cudaSuccess) e = cudaMemcpy(&I, ptr<InstDesc>(c->inst) + inst, sizeof I, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(basis, ptr<int64_t>(c->basis) + I.offBasis, sizeof(int64_t) * I.K * I.L, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_export_reduced");
+    return (msp_status)I.status;
+}
+
+msp_status msp_export_prefixes(msp_ctx* c, int inst, int32_t* u, double* rho, int64_t* nodes, int32_t* sols,
+                               size_t cap, size_t* count, int32_t* split_level) {
+    if (!c || !count) return MSP_EINVAL;
+    if (c->state < 3) return fail(c, MSP_ESTATE, "msp_export_prefixes before an enumeration");
+    if (inst < 0 || inst >= c->count) return fail(c, MSP_EINVAL, "instance index out of range");
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    InstDesc I;
+    if (e == cudaSuccess) e = cudaMemcpy(&I, ptr<InstDesc>(c->inst) + inst, sizeof I, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_export_prefixes");
+    *count = (size_t)I.nprefix;
+    if (split_level) *split_level = I.split_level;
+    const int64_t take = std::min<int64_t>(I.nprefix, (int64_t)cap);
+    const int64_t base = ((int64_t)inst * 2 + I.front_sel) * c->F;
+    if (u && take > 0) {
+        std::vector<int32_t> tmp((size_t)take * c->Kmax);
+        e = cudaMemcpy(tmp.data(), ptr<int32_t>(c->fu) + base * c->Kmax, sizeof(int32_t) * tmp.size(),
+                       cudaMemcpyDeviceToHost);
+        for (int64_t p = 0; p < take; ++p)
+            for (int i = 0; i < I.dd; ++i) u[(size_t)p * I.dd + i] = tmp[(size_t)p * c->Kmax + i];
+    }
+    if (e == cudaSuccess && rho && take > 0)
+        e = cudaMemcpy(rho, ptr<double>(c->frho) + base, sizeof(double) * take, cudaMemcpyDeviceToHost);
+    // the subtree log is indexed by queue position
+    if (e == cudaSuccess && (nodes || sols) && take > 0) {
+        int64_t q0 = 0;
+        e = cudaMemcpy(&q0, ptr<int64_t>(c->qbase) + inst, sizeof(int64_t), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && nodes)
+            e = cudaMemcpy(nodes, ptr<int64_t>(c->plog_nodes) + q0, sizeof(int64_t) * take, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && sols)
+            e = cudaMemcpy(sols, ptr<int32_t>(c->plog_sols) + q0, sizeof(int32_t) * take, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_export_prefixes copies");
+    return MSP_OK;
+}
+
+}  // extern "C"

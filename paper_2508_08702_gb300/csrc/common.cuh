@@ -1,0 +1,118 @@
+// common.cuh -- device-side data layout shared by the sm_103a kernels of the
+// market-split lattice solver.  Host orchestration lives in api.cu.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace msp {
+
+constexpr int kMaxM = 32;      // rows of A
+constexpr int kMaxDim = 128;   // n + 1 lattice coordinates after extraction
+constexpr int kMaxK = 128;     // basis vectors n + 1
+
+// per-instance status codes (same values as msp_status in include/msp.h)
+enum : int32_t {
+    ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_EOVERFLOW = 4, ST_ERANK = 5,
+    ST_ETIMEOUT = 6, ST_ETRUNC = 7, ST_ESTATE = 8, ST_ECAP = 9, ST_EQUEUE = 10
+};
+
+// Descriptor of one instance of a batch; offsets are element offsets into
+// the pools of Pools below.
+struct InstDesc {
+    int32_t m, n, K, L;      // K = n + 1 basis vectors of length L = m + n + 1
+    int32_t dd, dim;         // kernel rank (set by the extractor), dim = n + 1
+    int32_t status;
+    int32_t split_level;     // lowest level fixed by the splitter
+    int32_t front_sel;       // frontier buffer holding the final prefixes
+    int32_t pad0;
+    int64_t nprefix;         // number of prefixes (subtrees)
+    int64_t offA, offd;      // A (int32, m*n), d (int64, m)
+    int64_t offBasis;        // K*L int64   LLL basis, vector-major
+    int64_t offGram;         // K*K int64   exact Gram matrix
+    int64_t offMu;           // 2*K*K f64   LLL mu and r
+    int64_t offBl;           // K f64       LLL ||bhat||^2
+    int64_t offKb;           // K*dim int32 kept (kernel) basis
+    int64_t offMuT;          // K*K f64     muT[t][i] = mu[i][t]
+    int64_t offB;            // K f64       ||bhat_t||^2
+    int64_t offBhat;         // K*dim f64   bhat[t][c]
+    int64_t lll_iters, lll_swaps;
+};
+
+struct InstCounters {
+    unsigned long long nodes, passed, leaves, nsol;
+    unsigned long long split_nodes, split_passed;   // part done by the splitter
+    unsigned long long center_fma;                  // centre-fold fmas of the walkers
+};
+
+// A found solution: x_c is bit (127 - c) of the 128-bit key (hi:lo), so that
+// numeric key order equals lexicographic order of x as a byte string.
+struct SolRec {
+    int32_t inst;
+    int32_t pad;
+    unsigned long long hi, lo;
+};
+
+struct Pools {
+    InstDesc* inst;
+    InstCounters* cnt;
+    int count;
+    int Kmax, dimMax, dimPad;          // maxima over the batch; dimPad = dimMax rounded to 32
+    const int32_t* A;
+    const int64_t* d;
+    int64_t* basis;
+    int64_t* gram;
+    double* mu;
+    double* Bl;
+    int32_t* kb;
+    double* muT;
+    double* B;
+    double* bhat;
+    // splitter frontier: [count][2][F] prefixes of (u[Kmax] int32, rho, w[dimPad])
+    int32_t* fu;
+    double* frho;
+    double* fw;
+    int64_t F;
+    // work queue
+    int64_t* qbase;                    // count + 1 exclusive prefix sums of nprefix
+    const int64_t* qperm;              // optional queue order (learned); may be null
+    int64_t* plog_nodes;               // per prefix: nodes evaluated in its subtree
+    int32_t* plog_sols;                // per prefix: solutions found in its subtree
+    // solutions
+    SolRec* sols;
+    int64_t sol_cap;
+    struct Ctrl* ctrl;
+};
+
+// Control words of one enumeration, in device memory.
+struct Ctrl {
+    unsigned long long qhead;          // next static queue item
+    unsigned long long nsol_total;     // solutions found (all instances)
+    unsigned long long deadline_ns;    // globaltimer deadline, 0 = none
+    unsigned int stop;                 // 1: first solution found, 2: time cap
+    int32_t gstatus;                   // batch-wide status
+};
+
+// Enumeration options passed to the split and enumeration kernels.
+struct EnumCfg {
+    int hoelder;     // 0: Hoelder test with the one-direction cut, 1: skip value only, 2: off
+    int sym;         // 1: one of v, -v;  0: both signs
+    int use_eps;     // slack eps = (n+1) 2^-20 on both tests
+    int first;       // stop at the first solution
+};
+
+__device__ __forceinline__ int64_t frontier_index(const Pools& P, int inst, int sel, int64_t j) {
+    return ((int64_t)inst * 2 + sel) * P.F + j;
+}
+
+__device__ __forceinline__ unsigned long long global_time_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void set_status(InstDesc& I, int32_t st) {
+    atomicCAS(&I.status, ST_OK, st);
+}
+
+}  // namespace msp
