@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--lanes", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--instances", type=int, default=64,
+                   help="run only the first K instances of the batch (small profiling cases)")
     return p.parse_args()
 
 
@@ -198,7 +200,7 @@ def algorithmic_fp64_ops(stats, dims, lanes):
     sums and tree, slack add), plus the centre-fold fmas."""
     ops = 0
     for s, (m, n) in zip(stats, dims):
-        dim = n + 1
+        dim = int(n) + 1
         nodes = s["nodes"] - s["split_nodes"]
         inner = s["passed"] - s["split_passed"] - s["leaves"]
         ops += 3 * nodes + (2 * dim + int(math.log2(lanes)) + 1) * inner + s["center_fma"]
@@ -221,7 +223,7 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     # weak scaling: every rank runs its own batch of 64 (seeds shifted by rank)
-    insts = I.batch_m4_7(64, first_seed=2000 + 64 * rank)
+    insts = I.batch_m4_7(64, first_seed=2000 + 64 * rank)[:args.instances]
     pk = I.pack(insts)
     kw = {} if args.lanes is None else {"lanes": args.lanes}
     ctx = M.Context(**kw)
@@ -304,7 +306,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "instances": len(insts), "lanes": lanes,
+        "config": {"workload": WORKLOAD if len(insts) == 64 else f"first {len(insts)} instances of: {WORKLOAD}",
+                   "instances": len(insts), "lanes": lanes,
                    "l2": "flushed between steps (512 MB write)",
                    "nodes_per_step": res.total["nodes"], "solutions_per_step": res.total["solutions"],
                    "phase_ms": {k: round(v, 3) for k, v in ph.items()},

@@ -83,6 +83,8 @@ typedef struct {
     int64_t sol_capacity;  /* [1<<20] solutions stored (over all instances)               */
     double max_seconds;    /* [600] safety cap on every enumeration's device time; the     */
                            /*       walkers stop and report MSP_ETIMEOUT when it passes   */
+    int64_t donation_capacity; /* [1<<18] sibling ranges busy walkers may hand to idle */
+                           /*       ones during one enumeration (0: no donation)          */
 } msp_opts;
 
 /* Per-instance results of an enumeration. */

@@ -26,6 +26,7 @@ cudaError_t launch_collect(const Pools& P, int64_t* soff, unsigned long long* fi
                            cudaStream_t st);
 cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, cudaStream_t st);
 int64_t walker_bytes(int Kmax, int dimPad);
+int64_t donation_slot_bytes(int Kmax, int dimPad);
 int enum_blocks_per_sm(int lanes, int threads);
 cudaError_t fp64_peak(double* dfma_per_s, int sms, cudaStream_t st);
 }  // namespace msp
@@ -62,7 +63,7 @@ struct msp_ctx {
     bool reduce_timed = false;
     // device buffers
     Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, fu, frho, fw, fcnt, qbase, sols, ctrl, soff,
-        fill, seg, sout, scratch, plog_nodes, plog_sols;
+        fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_ready;
     std::vector<int64_t> soff_h;
     std::vector<SolRec> sout_h;
     bool sout_valid = false;
@@ -130,6 +131,10 @@ void refresh_pools(msp_ctx* c) {
     P.qperm = nullptr;
     P.plog_nodes = ptr<int64_t>(c->plog_nodes);
     P.plog_sols = ptr<int32_t>(c->plog_sols);
+    P.don = ptr<char>(c->don);
+    P.don_ready = ptr<unsigned int>(c->don_ready);
+    P.don_cap = c->o.donation_capacity;
+    P.don_stride = donation_slot_bytes(c->Kmax, c->dimPad);
     P.sols = ptr<SolRec>(c->sols);
     P.sol_cap = c->o.sol_capacity;
     P.ctrl = ptr<Ctrl>(c->ctrl);
@@ -173,6 +178,7 @@ void msp_default_opts(msp_opts* o) {
     o->smem_tables = 1;
     o->sol_capacity = 1 << 20;
     o->max_seconds = 600.0;
+    o->donation_capacity = 1 << 18;
 }
 
 const char* msp_status_string(int s) {
@@ -206,7 +212,7 @@ msp_status msp_create(msp_ctx** out, const msp_opts* opts, void* stream) {
     if (o.N < 1 || o.N > (1LL << 30) || !(o.delta > 0.25 && o.delta < 1.0) || !(o.eta >= 0.5 && o.eta < 1.0) ||
         o.hoelder < 0 || o.hoelder > 2 || (o.lanes != 8 && o.lanes != 16 && o.lanes != 32) ||
         o.split_depth < 0 || o.warps_per_block < 1 || o.warps_per_block > 8 || o.sol_capacity < 1 ||
-        o.lll_max_iter < 1 || !(o.max_seconds > 0.0)) {
+        o.lll_max_iter < 1 || !(o.max_seconds > 0.0) || o.donation_capacity < 0) {
         delete c;
         return MSP_EINVAL;
     }
@@ -233,7 +239,8 @@ void msp_destroy(msp_ctx* c) {
     cudaStreamSynchronize(c->st);
     Buf* all[] = {&c->inst, &c->cnt, &c->A, &c->d, &c->basis, &c->gram, &c->mu, &c->Bl, &c->kb, &c->muT, &c->B,
                   &c->bhat, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
-                  &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols};
+                  &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols, &c->don,
+                  &c->don_ready};
     for (Buf* b : all)
         if (b->p) cudaFree(b->p);
     for (cudaEvent_t ev : {c->ev0, c->ev1, c->evr0, c->evr1, c->evs1, c->eve1})
@@ -298,6 +305,8 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     ENSURE(fcnt, sizeof(int64_t) * (size_t)count * c->F);
     ENSURE(plog_nodes, sizeof(int64_t) * (size_t)count * c->F);
     ENSURE(plog_sols, sizeof(int32_t) * (size_t)count * c->F);
+    ENSURE(don, (size_t)c->o.donation_capacity * donation_slot_bytes(Kmax, c->dimPad));
+    ENSURE(don_ready, sizeof(unsigned int) * (size_t)c->o.donation_capacity);
     ENSURE(qbase, sizeof(int64_t) * (count + 1));
     ENSURE(sols, sizeof(SolRec) * (size_t)c->o.sol_capacity);
     ENSURE(ctrl, sizeof(Ctrl));
@@ -354,6 +363,7 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
     cudaError_t e = cudaMemsetAsync(c->cnt.p, 0, sizeof(InstCounters) * c->count, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->plog_nodes.p, 0, c->plog_nodes.bytes, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->plog_sols.p, 0, c->plog_sols.bytes, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->don_ready.p, 0, c->don_ready.bytes, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset counters");
     // the caller's cap, else the context's safety cap: no walk outlives it
     const double cap_s = time_cap_s > 0 ? std::min(time_cap_s, c->o.max_seconds) : c->o.max_seconds;

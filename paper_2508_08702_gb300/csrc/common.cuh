@@ -78,6 +78,10 @@ struct Pools {
     const int64_t* qperm;              // optional queue order (learned); may be null
     int64_t* plog_nodes;               // per prefix: nodes evaluated in its subtree
     int32_t* plog_sols;                // per prefix: solutions found in its subtree
+    // donated sibling ranges (work handed from busy walkers to idle ones)
+    char* don;                         // don_cap slots of don_stride bytes
+    unsigned int* don_ready;           // per slot: 1 once written
+    int64_t don_cap, don_stride;
     // solutions
     SolRec* sols;
     int64_t sol_cap;
@@ -87,6 +91,9 @@ struct Pools {
 // Control words of one enumeration, in device memory.
 struct Ctrl {
     unsigned long long qhead;          // next static queue item
+    unsigned long long dhead, dtail;   // donation queue: next to take / next free slot
+    int idle;                          // walkers waiting for donated work
+    int busy;                          // walkers holding work
     unsigned long long nsol_total;     // solutions found (all instances)
     unsigned long long deadline_ns;    // globaltimer deadline, 0 = none
     unsigned int stop;                 // 1: first solution found, 2: time cap

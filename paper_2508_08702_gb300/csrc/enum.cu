@@ -218,6 +218,10 @@ __global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int ma
 // resets the control words and arms the time cap on the device clock
 __global__ void start_kernel(Ctrl* c, unsigned long long cap_ns) {
     c->qhead = 0;
+    c->dhead = 0;
+    c->dtail = 0;
+    c->idle = 0;
+    c->busy = 0;
     c->nsol_total = 0;
     c->stop = 0;
     c->gstatus = 0;
@@ -248,11 +252,30 @@ struct WalkerLayout {
     }
 };
 
+// Header of a donated sibling range: the untried values at level t of a
+// walk, continued by another walker exactly where the donor stopped.  The
+// slot continues with int32 u[Kmax] (values above t) and double w[dimPad]
+// (w^(t+1)).
+struct DonHdr {
+    int32_t inst, t, u, u1, zi, meta;
+    int64_t gid;
+    double y, rhoP;
+};
+
+__host__ __device__ inline int64_t donation_stride(int Kmax, int dimPad) {
+    return ((int64_t)sizeof(DonHdr) + (int64_t)Kmax * 4 + 15) / 16 * 16 + (int64_t)dimPad * 8;
+}
+
 template <int G>
 __device__ __forceinline__ unsigned group_mask() {
     const int gi = (threadIdx.x & 31) / G;
     return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
 }
+
+// level meta bits
+constexpr int kOneDir = 1, kNegS = 2, kZeroPrefix = 4, kDonated = 8;
+// walk actions
+constexpr int kNext = 0, kDescend = 1, kUp = 2, kEval = 3;
 
 template <int G>
 __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* scratch, WalkerLayout W) {
@@ -271,65 +294,152 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
     double* lv_rhoP = lv_y + Kmax;
     double* wstack = lv_rhoP + Kmax;
     double* sigma = wstack + (int64_t)Kmax * dimPad;
+    Ctrl* ctrl = P.ctrl;
 
     const int64_t total = P.qbase[P.count];
+    bool static_done = false;   // meaningful in lane 0 only
     for (;;) {
-        unsigned long long item = 0;
-        if (lg == 0) item = atomicAdd(&P.ctrl->qhead, 1ULL);
-        item = __shfl_sync(gmask, item, 0, G);
-        if ((int64_t)item >= total) break;
-        int stopped = 0;
-        if (lg == 0) stopped = *(volatile unsigned*)&P.ctrl->stop != 0;
-        stopped = __shfl_sync(gmask, stopped, 0, G);
-        if (stopped) break;
-        int64_t gid = (int64_t)item;
-        if (P.qperm) gid = P.qperm[gid];
-        // instance of this prefix
-        int lo = 0, hi = P.count;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (P.qbase[mid] <= gid) lo = mid; else hi = mid;
+        // ---- obtain work: a split prefix, else a donated sibling range ----
+        int src = 0;
+        long long id = 0;
+        if (lg == 0) {
+            if (!static_done) {
+                const unsigned long long it = atomicAdd(&ctrl->qhead, 1ULL);
+                if ((int64_t)it < total) {
+                    src = 1;
+                    id = (long long)it;
+                    atomicAdd(&ctrl->busy, 1);
+                } else {
+                    static_done = true;
+                }
+            }
+            if (src == 0) {
+                atomicAdd(&ctrl->idle, 1);
+                for (;;) {
+                    if (*(volatile unsigned*)&ctrl->stop) break;
+                    const unsigned long long h = *(volatile unsigned long long*)&ctrl->dhead;
+                    const unsigned long long tl = *(volatile unsigned long long*)&ctrl->dtail;
+                    if (h < tl) {
+                        if (atomicCAS(&ctrl->dhead, h, h + 1) == h) {
+                            atomicAdd(&ctrl->busy, 1);
+                            src = 2;
+                            id = (long long)h;
+                            break;
+                        }
+                        continue;
+                    }
+                    if (*(volatile int*)&ctrl->busy == 0 &&
+                        *(volatile unsigned long long*)&ctrl->dhead == *(volatile unsigned long long*)&ctrl->dtail)
+                        break;   // nothing left anywhere
+                    if (global_time_ns() > ctrl->deadline_ns) {
+                        atomicExch(&ctrl->stop, 2u);
+                        break;
+                    }
+                    __nanosleep(1000);
+                }
+                atomicSub(&ctrl->idle, 1);
+            }
+            if (src == 2) {   // wait until the donor has written the slot
+                while (!*(volatile unsigned*)&P.don_ready[id]) {
+                    if (global_time_ns() > ctrl->deadline_ns) {
+                        atomicExch(&ctrl->stop, 2u);
+                        atomicSub(&ctrl->busy, 1);
+                        src = 0;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+                __threadfence();
+            }
         }
-        const int inst = lo;
+        src = __shfl_sync(gmask, src, 0, G);
+        id = __shfl_sync(gmask, id, 0, G);
+        if (src == 0) break;
+
+        // ---- set up the walk ----
+        int inst;
+        int64_t gid;
+        int t0;
+        double w_par[CPL], w_ch[CPL];
+        double rhoP, y = 0.0;
+        int u = 0, u1 = 0, s = 1, zi = 1, dir = 0;
+        bool onedir = false, zp = true;
+        int act;
+        if (src == 1) {
+            gid = P.qperm ? P.qperm[id] : (int64_t)id;
+            int lo = 0, hi = P.count;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (P.qbase[mid] <= gid) lo = mid; else hi = mid;
+            }
+            inst = lo;
+        } else {
+            const DonHdr* hd = reinterpret_cast<const DonHdr*>(P.don + id * P.don_stride);
+            inst = hd->inst;
+            gid = hd->gid;
+        }
         const InstDesc& I = P.inst[inst];
         const int dd = I.dd, dim = I.dim, n = I.n, m = I.m;
-        const int split_level = I.split_level;
-        const int t0 = split_level - 1;
         const double* __restrict__ muT = P.muT + I.offMuT;
         const double* __restrict__ Bt = P.B + I.offB;
         const double* __restrict__ bhat = P.bhat + I.offBhat;
         const int32_t* __restrict__ kb = P.kb + I.offKb;
         const double eps = slack_of(dim, cfg.use_eps);
         const double Rb = (double)dim + eps;
-        const int64_t fo = frontier_index(P, inst, I.front_sel, gid - P.qbase[inst]);
-
-        // subtree set-up from the prefix
-        const int32_t* pu = P.fu + fo * P.Kmax;
-        bool zp = true;
-        for (int i = split_level; i < dd; ++i) {
-            const int32_t v = pu[i];
-            lv_u[i] = v;
-            zp = zp && (v == 0);
+        if (src == 1) {
+            const int split_level = I.split_level;
+            t0 = split_level - 1;
+            const int64_t fo = frontier_index(P, inst, I.front_sel, gid - P.qbase[inst]);
+            const int32_t* pu = P.fu + fo * P.Kmax;
+            for (int i = split_level; i < dd; ++i) {
+                const int32_t v = pu[i];
+                lv_u[i] = v;
+                zp = zp && (v == 0);
+            }
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                const int c = lg + G * q;
+                w_par[q] = (c < dim) ? P.fw[fo * P.dimPad + c] : 0.0;
+            }
+            rhoP = P.frho[fo];
+            act = kEval;   // fresh level: enter it below
+        } else {
+            const char* slot = P.don + id * P.don_stride;
+            const DonHdr hd = *reinterpret_cast<const DonHdr*>(slot);
+            const int32_t* su = reinterpret_cast<const int32_t*>(slot + sizeof(DonHdr));
+            const double* sw = reinterpret_cast<const double*>(
+                slot + ((int64_t)sizeof(DonHdr) + (int64_t)Kmax * 4 + 15) / 16 * 16);
+            t0 = hd.t;
+            for (int i = t0 + 1; i < dd; ++i) lv_u[i] = su[i];
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                const int c = lg + G * q;
+                w_par[q] = (c < dim) ? sw[c] : 0.0;
+            }
+            rhoP = hd.rhoP;
+            y = hd.y;
+            u = hd.u;
+            u1 = hd.u1;
+            onedir = hd.meta & kOneDir;
+            s = (hd.meta & kNegS) ? -1 : 1;
+            zp = (hd.meta & kZeroPrefix) != 0;
+            if (onedir) dir = hd.zi; else zi = hd.zi;
+            act = kNext;   // the donor evaluated u already
         }
-        for (int i = lg; i < split_level; i += G) lv_J[i] = dd - 1;
+        for (int i = lg; i <= t0; i += G) lv_J[i] = dd - 1;
         for (int i = lg; i < dd; i += G) sigma[(int64_t)i * S + dd] = 0.0;
-        double w_par[CPL], w_ch[CPL];
 #pragma unroll
         for (int q = 0; q < CPL; ++q) {
             const int c = lg + G * q;
-            w_par[q] = (c < dim) ? P.fw[fo * P.dimPad + c] : 0.0;
             w_ch[q] = 0.0;
             if (c < dim) wstack[(int64_t)t0 * dimPad + c] = w_par[q];
         }
-        double rhoP = P.frho[fo];
+        if (lg == 0) lv_meta[t0] = 0;
         __syncwarp(gmask);
 
         unsigned long long nodes = 0, passed = 0, leaves = 0, cfma = 0;
         int item_sols = 0;
         int t = t0;
-        double y = 0.0;
-        int u = 0, u1 = 0, s = 1, zi = 1, dir = 0;
-        bool onedir = false;
         bool abort = false;
 
         // entering level t: centre by the cached fold, start of the zig-zag
@@ -354,28 +464,74 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
             u = u1;
             if (t > 0) lv_J[t - 1] = max(lv_J[t - 1], t);
         };
-        enter_level();
+        if (src == 1) enter_level();
 
         while (!abort) {
+            if (act == kNext) {
+                if (onedir) u += dir;
+                else { ++zi; u = zigzag(u1, s, zi); }
+                if (t > 0) lv_J[t - 1] = max(lv_J[t - 1], t);
+            }
             if ((nodes & 1023) == 1023) {
-                int st = 0;
+                // stop flag, time cap, and donation to idle walkers
+                int st = 0, want = 0;
                 if (lg == 0) {
-                    st = *(volatile unsigned*)&P.ctrl->stop != 0;
-                    if (!st && P.ctrl->deadline_ns && global_time_ns() > P.ctrl->deadline_ns) {
-                        atomicExch(&P.ctrl->stop, 2u);
+                    st = *(volatile unsigned*)&ctrl->stop != 0;
+                    if (!st && global_time_ns() > ctrl->deadline_ns) {
+                        atomicExch(&ctrl->stop, 2u);
                         st = 1;
+                    }
+                    const int idle = *(volatile int*)&ctrl->idle;
+                    if (idle > 0) {
+                        const unsigned long long q = *(volatile unsigned long long*)&ctrl->dtail -
+                                                     *(volatile unsigned long long*)&ctrl->dhead;
+                        want = q < (unsigned long long)idle;
                     }
                 }
                 if (__shfl_sync(gmask, st, 0, G)) { abort = true; break; }
+                if (__shfl_sync(gmask, want, 0, G)) {
+                    int h = -1;
+                    for (int l = t0; l > t; --l)
+                        if (!(lv_meta[l] & kDonated)) { h = l; break; }
+                    if (h >= 0) {
+                        long long slot = -1;
+                        if (lg == 0) {
+                            for (int tries = 0; tries < 64; ++tries) {
+                                const unsigned long long old = *(volatile unsigned long long*)&ctrl->dtail;
+                                if ((int64_t)old >= P.don_cap) break;
+                                if (atomicCAS(&ctrl->dtail, old, old + 1) == old) { slot = (long long)old; break; }
+                            }
+                        }
+                        slot = __shfl_sync(gmask, slot, 0, G);
+                        if (slot >= 0) {
+                            char* sp = P.don + slot * P.don_stride;
+                            int32_t* su = reinterpret_cast<int32_t*>(sp + sizeof(DonHdr));
+                            double* sw = reinterpret_cast<double*>(
+                                sp + ((int64_t)sizeof(DonHdr) + (int64_t)Kmax * 4 + 15) / 16 * 16);
+                            if (lg == 0) {
+                                DonHdr hd;
+                                hd.inst = inst; hd.t = h; hd.u = lv_u[h]; hd.u1 = lv_u1[h];
+                                hd.zi = lv_zi[h]; hd.meta = lv_meta[h] & ~kDonated; hd.gid = gid;
+                                hd.y = lv_y[h]; hd.rhoP = lv_rhoP[h];
+                                *reinterpret_cast<DonHdr*>(sp) = hd;
+                            }
+                            for (int i = h + 1 + lg; i < dd; i += G) su[i] = lv_u[i];
+                            for (int c = lg; c < dim; c += G) sw[c] = wstack[(int64_t)h * dimPad + c];
+                            __threadfence();
+                            __syncwarp(gmask);
+                            if (lg == 0) atomicExch(&P.don_ready[slot], 1u);
+                            lv_meta[h] |= kDonated;
+                            __syncwarp(gmask);
+                        }
+                    }
+                }
             }
             if (u >= kUMax || u <= -kUMax) { abort = true; set_status(const_cast<InstDesc&>(I), ST_EOVERFLOW); break; }
             const double x = __dadd_rn((double)u, y);
             const double rho = __fma_rn(__dmul_rn(x, x), Bt[t], rhoP);
             ++nodes;
-            // 0 = next value, 1 = descend, 2 = step back, 3 = evaluate the new u
-            int act;
             if (!(rho <= Rb)) {   // norm test (a NaN never passes)
-                act = 2;
+                act = kUp;
             } else {
                 ++passed;
                 if (t == 0) {
@@ -435,18 +591,18 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
                         }
                         ok = __all_sync(gmask, ok);
                         if (ok && lg == 0) {
-                            const unsigned long long k = atomicAdd(&P.ctrl->nsol_total, 1ULL);
+                            const unsigned long long k = atomicAdd(&ctrl->nsol_total, 1ULL);
                             if ((int64_t)k < P.sol_cap) {
                                 SolRec r;
                                 r.inst = inst; r.pad = 0; r.hi = khi; r.lo = klo;
                                 P.sols[k] = r;
                             }
                             atomicAdd(&P.cnt[inst].nsol, 1ULL);
-                            if (cfg.first) atomicExch(&P.ctrl->stop, 1u);
+                            if (cfg.first) atomicExch(&ctrl->stop, 1u);
                         }
                         if (ok) ++item_sols;
                     }
-                    act = 0;
+                    act = kNext;
                 } else {
                     double sl = 0.0;
 #pragma unroll
@@ -464,27 +620,27 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
                     if (cfg.hoelder != HOELDER_OFF) fail = rho > __dadd_rn(sl, eps);
                     if (fail && cfg.hoelder == HOELDER_CUT) {
                         if (onedir) {
-                            act = 2;
+                            act = kUp;
                         } else {
+                            // first failure: one more regular value, then one direction
                             ++zi;
                             u = zigzag(u1, s, zi);
                             dir = (u > u1) ? 1 : -1;
                             onedir = true;
                             lv_J[t - 1] = max(lv_J[t - 1], t);
-                            act = 3;
+                            act = kEval;
                         }
                     } else {
-                        act = fail ? 0 : 1;
+                        act = fail ? kNext : kDescend;
                     }
                 }
             }
-            if (act == 3) continue;
-            if (act == 1) {
+            if (act == kDescend) {
                 // save level t, make the child the parent of level t-1
                 lv_u[t] = u;
                 lv_u1[t] = u1;
                 lv_zi[t] = onedir ? dir : zi;
-                lv_meta[t] = (onedir ? 1 : 0) | (s < 0 ? 2 : 0) | (zp ? 4 : 0);
+                lv_meta[t] = (onedir ? kOneDir : 0) | (s < 0 ? kNegS : 0) | (zp ? kZeroPrefix : 0);
                 lv_y[t] = y;
                 lv_rhoP[t] = rhoP;
 #pragma unroll
@@ -498,17 +654,24 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
                 --t;
                 __syncwarp(gmask);
                 enter_level();
+                act = kEval;
                 continue;
             }
-            if (act == 2) {
-                if (t == t0) break;
-                ++t;
+            if (act == kUp) {
+                // step back; levels whose remaining values were donated are done
+                bool done = false;
+                int meta = 0;
+                do {
+                    if (t == t0) { done = true; break; }
+                    ++t;
+                    meta = lv_meta[t];
+                } while (meta & kDonated);
+                if (done) break;
                 u = lv_u[t];
                 u1 = lv_u1[t];
-                const int meta = lv_meta[t];
-                onedir = meta & 1;
-                s = (meta & 2) ? -1 : 1;
-                zp = (meta & 4) != 0;
+                onedir = meta & kOneDir;
+                s = (meta & kNegS) ? -1 : 1;
+                zp = (meta & kZeroPrefix) != 0;
                 if (onedir) dir = lv_zi[t]; else zi = lv_zi[t];
                 y = lv_y[t];
                 rhoP = lv_rhoP[t];
@@ -518,25 +681,23 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
                     w_par[q] = (c < dim) ? wstack[(int64_t)t * dimPad + c] : 0.0;
                 }
                 __syncwarp(gmask);
+                act = kNext;
             }
-            // next value at level t
-            if (onedir) u += dir;
-            else { ++zi; u = zigzag(u1, s, zi); }
-            if (t > 0) lv_J[t - 1] = max(lv_J[t - 1], t);
         }
-        if (abort && lg == 0 && !(*(volatile unsigned*)&P.ctrl->stop)) set_status(const_cast<InstDesc&>(I), ST_EOVERFLOW);
+        if (abort && lg == 0 && !(*(volatile unsigned*)&ctrl->stop)) set_status(const_cast<InstDesc&>(I), ST_EOVERFLOW);
         if (lg == 0) {
             atomicAdd(&P.cnt[inst].nodes, nodes);
             atomicAdd(&P.cnt[inst].passed, passed);
             atomicAdd(&P.cnt[inst].leaves, leaves);
             atomicAdd(&P.cnt[inst].center_fma, cfma);
-            P.plog_nodes[gid] = abort ? -(int64_t)nodes : (int64_t)nodes;
-            P.plog_sols[gid] = item_sols;
+            atomicAdd(reinterpret_cast<unsigned long long*>(&P.plog_nodes[gid]), nodes);
+            if (item_sols) atomicAdd(&P.plog_sols[gid], item_sols);
+            atomicSub(&ctrl->busy, 1);
         }
         __syncwarp(gmask);
         if (abort) {
             int st = 0;
-            if (lg == 0) st = *(volatile unsigned*)&P.ctrl->stop != 0;
+            if (lg == 0) st = *(volatile unsigned*)&ctrl->stop != 0;
             if (__shfl_sync(gmask, st, 0, G)) break;
         }
     }
@@ -621,6 +782,8 @@ int enum_blocks_per_sm(int lanes, int threads) {
 }
 
 int64_t walker_bytes(int Kmax, int dimPad) { return WalkerLayout{Kmax, dimPad}.bytes(); }
+
+int64_t donation_slot_bytes(int Kmax, int dimPad) { return donation_stride(Kmax, dimPad); }
 
 cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
                         int Kmax, int dimPad, cudaStream_t st) {
