@@ -70,7 +70,7 @@ typedef struct {
     int sym;               /* [1] 1: enumerate one of v, -v (first nonzero u > 0);        */
                            /*     0: both signs, keep leaves whose last entry is +1       */
     int use_eps;           /* [1] slack eps = (n+1) 2^-20 on both tests (0: none)         */
-    int lanes;             /* [16] lanes per subtree walker: 8, 16 or 32.  Also fixes the */
+    int lanes;             /* [8] lanes per subtree walker: 4, 8, 16 or 32.  Also fixes the */
                            /*      summation order of ||w||_1 (G interleaved partial sums */
                            /*      combined pairwise), so node counts depend on it        */
     int split_depth;       /* [24] maximum number of top levels the splitter expands      */
@@ -102,6 +102,8 @@ typedef struct {
     int64_t split_nodes;   /* part of `nodes` evaluated by the splitter               */
     int64_t split_passed;  /* part of `passed` evaluated by the splitter              */
     int64_t center_fma;    /* fmas spent by the walkers on the centres y_t            */
+    int64_t fallbacks;     /* Hoelder tests too close to call from the exact integer  */
+                           /* filter, decided by rebuilding the FP64 vector           */
     int32_t status;        /* msp_status of this instance                              */
     int32_t reserved;
     double ms;             /* wall time of the enumeration call (whole batch)          */

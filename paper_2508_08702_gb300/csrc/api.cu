@@ -18,6 +18,7 @@ namespace msp {
 __global__ void build_lattice_kernel(Pools P, int64_t N);
 __global__ void lll_kernel(Pools P, double delta, double eta, int64_t max_iter, unsigned long long max_ns);
 __global__ void extract_gso_kernel(Pools P);
+__global__ void prep_fixed_kernel(Pools P, int use_eps, int dimPad);
 cudaError_t launch_split(const Pools& P, const EnumCfg& cfg, int lanes, int max_depth, int64_t target,
                          int64_t* fcnt, cudaStream_t st);
 cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
@@ -27,7 +28,8 @@ cudaError_t launch_collect(const Pools& P, int64_t* soff, unsigned long long* fi
 cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, cudaStream_t st);
 int64_t walker_bytes(int Kmax, int dimPad);
 int64_t donation_slot_bytes(int Kmax, int dimPad);
-int enum_blocks_per_sm(int lanes, int threads);
+int enum_blocks_per_sm(int lanes, int threads, int dimMax, int Kmax);
+int enum_smem_bytes(int lanes, int threads, int Kmax);
 cudaError_t fp64_peak(double* dfma_per_s, int sms, cudaStream_t st);
 }  // namespace msp
 
@@ -62,7 +64,7 @@ struct msp_ctx {
     cudaEvent_t evs1 = nullptr, eve1 = nullptr;   // split end, enumerate end
     bool reduce_timed = false;
     // device buffers
-    Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, fu, frho, fw, fcnt, qbase, sols, ctrl, soff,
+    Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, bq, nbq, fu, frho, fw, fcnt, qbase, sols, ctrl, soff,
         fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_ready;
     std::vector<int64_t> soff_h;
     std::vector<SolRec> sout_h;
@@ -123,6 +125,8 @@ void refresh_pools(msp_ctx* c) {
     P.muT = ptr<double>(c->muT);
     P.B = ptr<double>(c->B);
     P.bhat = ptr<double>(c->bhat);
+    P.bq = ptr<int32_t>(c->bq);
+    P.nbq = ptr<int64_t>(c->nbq);
     P.fu = ptr<int32_t>(c->fu);
     P.frho = ptr<double>(c->frho);
     P.fw = ptr<double>(c->fw);
@@ -145,7 +149,7 @@ int walkers_of(const msp_ctx* c, int blocks, int threads) { return blocks * thre
 void enum_launch_shape(const msp_ctx* c, int* blocks, int* threads) {
     *threads = c->o.warps_per_block * 32;
     int bps = c->o.blocks_per_sm;
-    if (bps <= 0) bps = std::max(1, enum_blocks_per_sm(c->o.lanes, *threads));
+    if (bps <= 0) bps = std::max(1, enum_blocks_per_sm(c->o.lanes, *threads, c->dimMax, c->Kmax));
     *blocks = c->sms * bps;
 }
 
@@ -169,7 +173,7 @@ void msp_default_opts(msp_opts* o) {
     o->hoelder = 0;
     o->sym = 1;
     o->use_eps = 1;
-    o->lanes = 16;
+    o->lanes = 8;
     o->split_depth = 24;
     o->split_target = 0;
     o->split_capacity = 0;
@@ -210,7 +214,7 @@ msp_status msp_create(msp_ctx** out, const msp_opts* opts, void* stream) {
     if (opts) c->o = *opts; else msp_default_opts(&c->o);
     const msp_opts& o = c->o;
     if (o.N < 1 || o.N > (1LL << 30) || !(o.delta > 0.25 && o.delta < 1.0) || !(o.eta >= 0.5 && o.eta < 1.0) ||
-        o.hoelder < 0 || o.hoelder > 2 || (o.lanes != 8 && o.lanes != 16 && o.lanes != 32) ||
+        o.hoelder < 0 || o.hoelder > 2 || (o.lanes != 4 && o.lanes != 8 && o.lanes != 16 && o.lanes != 32) ||
         o.split_depth < 0 || o.warps_per_block < 1 || o.warps_per_block > 8 || o.sol_capacity < 1 ||
         o.lll_max_iter < 1 || !(o.max_seconds > 0.0) || o.donation_capacity < 0) {
         delete c;
@@ -238,7 +242,7 @@ void msp_destroy(msp_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->st);
     Buf* all[] = {&c->inst, &c->cnt, &c->A, &c->d, &c->basis, &c->gram, &c->mu, &c->Bl, &c->kb, &c->muT, &c->B,
-                  &c->bhat, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
+                  &c->bhat, &c->bq, &c->nbq, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
                   &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols, &c->don,
                   &c->don_ready};
     for (Buf* b : all)
@@ -278,6 +282,12 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     c->Kmax = Kmax;
     c->dimMax = dimMax;
     c->dimPad = (dimMax + 31) / 32 * 32;
+    int64_t nBq = 0;
+    for (int i = 0; i < count; ++i) {
+        h[i].offBq = nBq;
+        h[i].offNbq = (int64_t)i * Kmax;
+        nBq += (int64_t)h[i].K * c->dimPad;
+    }
     // split sizes
     int blocks, threads;
     enum_launch_shape(c, &blocks, &threads);
@@ -299,6 +309,8 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     ENSURE(muT, sizeof(double) * nT);
     ENSURE(B, sizeof(double) * nK);
     ENSURE(bhat, sizeof(double) * nKb);
+    ENSURE(bq, sizeof(int32_t) * nBq);
+    ENSURE(nbq, sizeof(int64_t) * (size_t)count * Kmax);
     ENSURE(fu, sizeof(int32_t) * (size_t)count * 2 * c->F * Kmax);
     ENSURE(frho, sizeof(double) * (size_t)count * 2 * c->F);
     ENSURE(fw, sizeof(double) * (size_t)count * 2 * c->F * c->dimPad);
@@ -344,6 +356,9 @@ msp_status msp_reduce(msp_ctx* c) {
     extract_gso_kernel<<<c->count, 32, 0, c->st>>>(c->P);
     ++c->launches;
     if ((s = check_launch(c, "extract_gso_kernel")) != MSP_OK) return s;
+    prep_fixed_kernel<<<c->count, 32, 0, c->st>>>(c->P, c->o.use_eps, c->dimPad);
+    ++c->launches;
+    if ((s = check_launch(c, "prep_fixed_kernel")) != MSP_OK) return s;
     cudaEventRecord(c->evr1, c->st);
     c->reduce_timed = true;
     c->state = 2;
@@ -438,6 +453,7 @@ msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {
         S.split_nodes = (int64_t)cn[i].split_nodes;
         S.split_passed = (int64_t)cn[i].split_passed;
         S.center_fma = (int64_t)cn[i].center_fma;
+        S.fallbacks = (int64_t)cn[i].fallbacks;
         int32_t st = h[i].status;
         if (st == MSP_OK && ctl.stop == 2) st = MSP_ETIMEOUT;
         if (st == MSP_OK && trunc) st = MSP_ETRUNC;
@@ -454,6 +470,7 @@ msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {
         tot.split_nodes += S.split_nodes;
         tot.split_passed += S.split_passed;
         tot.center_fma += S.center_fma;
+        tot.fallbacks += S.fallbacks;
     }
     tot.status = first_bad;
     tot.ms = ms;

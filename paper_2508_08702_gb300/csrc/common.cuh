@@ -37,12 +37,17 @@ struct InstDesc {
     int64_t offB;            // K f64       ||bhat_t||^2
     int64_t offBhat;         // K*dim f64   bhat[t][c]
     int64_t lll_iters, lll_swaps;
+    // fixed-point filter of the Hoelder test (set by prep_fixed_kernel)
+    int32_t sx, sb;          // scales: Xq = trunc(x 2^sx), Bq = round(bhat 2^sb)
+    int64_t offBq;           // K*dimPad int32   Bq[t][c]
+    int64_t offNbq;          // K int64          sum_c |Bq[t][c]|
 };
 
 struct InstCounters {
     unsigned long long nodes, passed, leaves, nsol;
     unsigned long long split_nodes, split_passed;   // part done by the splitter
     unsigned long long center_fma;                  // centre-fold fmas of the walkers
+    unsigned long long fallbacks;                   // Hoelder tests decided by the FP64 rebuild
 };
 
 // A found solution: x_c is bit (127 - c) of the 128-bit key (hi:lo), so that
@@ -68,6 +73,8 @@ struct Pools {
     double* muT;
     double* B;
     double* bhat;
+    int32_t* bq;                       // fixed-point bhat (see InstDesc::offBq)
+    int64_t* nbq;
     // splitter frontier: [count][2][F] prefixes of (u[Kmax] int32, rho, w[dimPad])
     int32_t* fu;
     double* frho;

@@ -29,7 +29,7 @@
 namespace msp {
 
 enum { HOELDER_CUT = 0, HOELDER_FILTER = 1, HOELDER_OFF = 2 };
-constexpr int kUMax = 1 << 20;   // |u| bound keeping integer leaf sums exact
+constexpr int kUMax = 1 << 15;   // |u| bound: levels store u as int16
 
 __device__ __forceinline__ int zigzag(int u1, int s, int i) {
     return (i & 1) == 0 ? u1 + s * (i >> 1) : u1 - s * ((i - 1) >> 1);
@@ -243,19 +243,48 @@ __global__ void queue_kernel(Pools P) {
 // Enumerator: persistent walkers of G lanes.
 // ---------------------------------------------------------------------------
 
+// Global scratch of one walker: the FP64 root vector w^(t0+1) of its walk
+// (the canonical start of the exact fallback) and the centre cache sigma.
 struct WalkerLayout {
     int Kmax, dimPad;
     __host__ __device__ int64_t bytes() const {
-        // level state: 5 int32 arrays + 2 double arrays; w stack; sigma cache
-        const int64_t ints = ((int64_t)5 * Kmax * 4 + 15) / 16 * 16;
-        return ints + (int64_t)2 * Kmax * 8 + (int64_t)Kmax * dimPad * 8 + (int64_t)Kmax * (Kmax + 1) * 8;
+        return (int64_t)dimPad * 8 + (int64_t)Kmax * (Kmax + 1) * 8;
     }
 };
 
+// Level state of one walker in shared memory: for each level t on the
+// current path, the value u being explored there, the zig-zag state, the
+// quantised x, the centre y_t and the parent's norm rho_{t+1}.
+struct Levels {
+    double* y;
+    double* rho;
+    int* xq;
+    short* u;
+    short* u1;
+    short* zi;
+    unsigned char* meta;
+    unsigned char* J;
+};
+
+__host__ __device__ inline int level_bytes(int Kmax) { return (Kmax * 28 + 15) / 16 * 16; }
+
+__device__ __forceinline__ Levels levels_at(unsigned char* base, int Kmax) {
+    Levels L;
+    L.y = reinterpret_cast<double*>(base);
+    L.rho = L.y + Kmax;
+    L.xq = reinterpret_cast<int*>(L.rho + Kmax);
+    L.u = reinterpret_cast<short*>(L.xq + Kmax);
+    L.u1 = L.u + Kmax;
+    L.zi = L.u1 + Kmax;
+    L.meta = reinterpret_cast<unsigned char*>(L.zi + Kmax);
+    L.J = L.meta + Kmax;
+    return L;
+}
+
 // Header of a donated sibling range: the untried values at level t of a
 // walk, continued by another walker exactly where the donor stopped.  The
-// slot continues with int32 u[Kmax] (values above t) and double w[dimPad]
-// (w^(t+1)).
+// slot continues with int32 u[Kmax] (values above t) and the canonical FP64
+// w^(t+1) (double[dimPad]).
 struct DonHdr {
     int32_t inst, t, u, u1, zi, meta;
     int64_t gid;
@@ -272,28 +301,209 @@ __device__ __forceinline__ unsigned group_mask() {
     return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
 }
 
+// exact int -> double without the FP64 pipe (|v| < 2^31)
+__device__ __forceinline__ double i2d_exact(int v) {
+    if (v == 0) return 0.0;
+    const unsigned a = v < 0 ? (unsigned)(-v) : (unsigned)v;
+    const int lz = __clz(a);
+    const unsigned long long m = ((unsigned long long)a << (lz + 21)) & 0x000fffffffffffffULL;
+    const unsigned long long bits = ((unsigned long long)(v < 0) << 63) |
+                                    ((unsigned long long)(1023 + 31 - lz) << 52) | m;
+    return __longlong_as_double((long long)bits);
+}
+
+// trunc(|x| 2^s) with the sign of x, by integer operations on the bits
+__device__ __forceinline__ long long fix_trunc(double x, int s) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const long long mant = (b & 0x000fffffffffffffLL) | 0x0010000000000000LL;
+    const int sh = 1075 - s - e;
+    long long q;
+    if (e == 0 || sh >= 63) q = 0;
+    else if (sh <= 0) q = mant << (-sh);
+    else q = mant >> sh;
+    return b < 0 ? -q : q;
+}
+
 // level meta bits
 constexpr int kOneDir = 1, kNegS = 2, kZeroPrefix = 4, kDonated = 8;
+
+// Rare paths of the walk, kept out of line so that they do not raise the
+// register pressure of the hot loop.
+
+// Exact Theorem 1 check of v = sum_j u_j b_j at a leaf (t = 0, u_0 = u);
+// records a verified solution.  Returns 1 if it was one.
+template <int G, int CPL>
+__device__ __noinline__ int leaf_check(const Pools& P, const EnumCfg& cfg, int inst, const Levels& L, int u,
+                                       unsigned gmask) {
+    const InstDesc& I = P.inst[inst];
+    const int dd = I.dd, dim = I.dim, n = I.n, m = I.m;
+    const int32_t* __restrict__ kb = P.kb + I.offKb;
+    const int lg = threadIdx.x & (G - 1);
+    long long v[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        const int c = lg + G * q;
+        long long a = 0;
+        if (c < dim) {
+            a = (long long)u * kb[c];
+            for (int j = 1; j < dd; ++j) a += (long long)L.u[j] * kb[(int64_t)j * dim + c];
+        }
+        v[q] = a;
+    }
+    long long mine = 0;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) if (q == (dim - 1) / G) mine = v[q];
+    const long long last = __shfl_sync(gmask, mine, (dim - 1) % G, G);
+    const long long sg = (cfg.sym && last == -1) ? -1 : 1;
+    bool ok = (last * sg == 1);
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        const int c = lg + G * q;
+        const long long vc = v[q] * sg;
+        if (c < n && vc != 1 && vc != -1) ok = false;
+    }
+    ok = __all_sync(gmask, ok);
+    if (!ok) return 0;
+    unsigned long long khi = 0, klo = 0;
+    const int gi = (threadIdx.x & 31) / G;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        const int c = lg + G * q;
+        const bool one = (c < n) && (v[q] * sg == 1);
+        unsigned bits = __ballot_sync(gmask, one) >> (gi * G);
+        if (G < 32) bits &= (1u << (G & 31)) - 1u;
+        for (int l = 0; l < G; ++l) {
+            if ((bits >> l) & 1u) {
+                const int cc = G * q + l;   // x_cc = 1 at key bit 127 - cc
+                if (cc < 64) khi |= 1ULL << (63 - cc);
+                else klo |= 1ULL << (127 - cc);
+            }
+        }
+    }
+    // independent verification A x = d
+    const int32_t* Ai = P.A + I.offA;
+    const int64_t* di = P.d + I.offd;
+    for (int i = lg; i < m; i += G) {
+        long long acc = 0;
+        for (int c = 0; c < n; ++c) {
+            const bool xc = c < 64 ? (khi >> (63 - c)) & 1ULL : (klo >> (127 - c)) & 1ULL;
+            if (xc) acc += Ai[(int64_t)i * n + c];
+        }
+        if (acc != di[i]) ok = false;
+    }
+    ok = __all_sync(gmask, ok);
+    if (ok && lg == 0) {
+        const unsigned long long k = atomicAdd(&P.ctrl->nsol_total, 1ULL);
+        if ((int64_t)k < P.sol_cap) {
+            SolRec r;
+            r.inst = inst; r.pad = 0; r.hi = khi; r.lo = klo;
+            P.sols[k] = r;
+        }
+        atomicAdd(&P.cnt[inst].nsol, 1ULL);
+        if (cfg.first) atomicExch(&P.ctrl->stop, 1u);
+    }
+    return ok ? 1 : 0;
+}
+
+// Canonical FP64 ||w^(t)||_1 for the node (t, x): the chain of Algorithm 1
+// rebuilt from the walk's root w^(t0+1) with the same fmas as the FP64
+// method, summed in the G-lane order.
+template <int G, int CPL>
+__device__ __noinline__ double canonical_l1(const double* __restrict__ bhat, const double* __restrict__ root_w,
+                                            const Levels& L, int t0, int t, double x, int dim, unsigned gmask) {
+    const int lg = threadIdx.x & (G - 1);
+    double sl = 0.0;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        const int c = lg + G * q;
+        if (c < dim) {
+            double w = root_w[c];
+            for (int j = t0; j > t; --j)
+                w = __fma_rn(__dadd_rn(i2d_exact(L.u[j]), L.y[j]), bhat[(int64_t)j * dim + c], w);
+            w = __fma_rn(x, bhat[(int64_t)t * dim + c], w);
+            sl = __dadd_rn(sl, fabs(w));
+        }
+    }
+#pragma unroll
+    for (int off = G / 2; off >= 1; off >>= 1) sl = __dadd_rn(sl, __shfl_xor_sync(gmask, sl, off, G));
+    return sl;
+}
+
+// Hand the untried values of the highest open level h in (t, t0] to an idle
+// walker.  Returns 1 if a slot was written.
+template <int G>
+__device__ __noinline__ int donate(const Pools& P, int inst, int64_t gid, const Levels& L, const double* root_w,
+                                   const double* __restrict__ bhat, int t0, int t, int dd, int dim, int Kmax,
+                                   unsigned gmask) {
+    const int lg = threadIdx.x & (G - 1);
+    int h = -1;
+    for (int l = t0; l > t; --l)
+        if (!(L.meta[l] & kDonated)) { h = l; break; }
+    if (h < 0) return 0;
+    long long slot = -1;
+    if (lg == 0) {
+        for (int tries = 0; tries < 64; ++tries) {
+            const unsigned long long old = *(volatile unsigned long long*)&P.ctrl->dtail;
+            if ((int64_t)old >= P.don_cap) break;
+            if (atomicCAS(&P.ctrl->dtail, old, old + 1) == old) { slot = (long long)old; break; }
+        }
+    }
+    slot = __shfl_sync(gmask, slot, 0, G);
+    if (slot < 0) return 0;
+    char* sp = P.don + slot * P.don_stride;
+    int32_t* su = reinterpret_cast<int32_t*>(sp + sizeof(DonHdr));
+    double* sw = reinterpret_cast<double*>(sp + ((int64_t)sizeof(DonHdr) + (int64_t)Kmax * 4 + 15) / 16 * 16);
+    if (lg == 0) {
+        DonHdr hd;
+        hd.inst = inst; hd.t = h; hd.u = L.u[h]; hd.u1 = L.u1[h];
+        hd.zi = L.zi[h]; hd.meta = L.meta[h] & ~kDonated; hd.gid = gid;
+        hd.y = L.y[h]; hd.rhoP = L.rho[h];
+        *reinterpret_cast<DonHdr*>(sp) = hd;
+    }
+    for (int i = h + 1 + lg; i < dd; i += G) su[i] = L.u[i];
+    // canonical FP64 w^(h+1): the chain from the root down to level h+1
+    for (int c = lg; c < dim; c += G) {
+        double w = root_w[c];
+        for (int j = t0; j > h; --j)
+            w = __fma_rn(__dadd_rn(i2d_exact(L.u[j]), L.y[j]), bhat[(int64_t)j * dim + c], w);
+        sw[c] = w;
+    }
+    __threadfence();
+    __syncwarp(gmask);
+    if (lg == 0) {
+        atomicExch(&P.don_ready[slot], 1u);
+        L.meta[h] |= kDonated;
+    }
+    __syncwarp(gmask);
+    return 1;
+}
 // walk actions
 constexpr int kNext = 0, kDescend = 1, kUp = 2, kEval = 3;
 
-template <int G>
-__global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* scratch, WalkerLayout W) {
-    constexpr int CPL = kMaxDim / G;
+// The walk state machine of one group of G lanes.  Lane l owns the
+// coordinates c = l + G q (q < CPL) of the integer vector
+//   W = sum_j Xq_j Bq_j  ~  w^(t+1) 2^(sx+sb),
+// exact and therefore reversible: stepping back to level t subtracts that
+// level's term instead of reloading a stored vector.  E bounds (in units of
+// 2^-(sx+sb)) the distance of ||W||_1 from the exact ||w||_1:
+//   per level: (n+1)(|Xq| + 1)/2 + sum_c |Bq_c| + 1, plus (n+1) for rounding the root.
+// The Hoelder decision of the FP64 method, rho > ||w||_1 + eps, is taken from
+// W whenever the margin exceeds the bound; otherwise the canonical FP64 w is
+// rebuilt from the walk's root and the decision is taken exactly as the
+// FP64 arithmetic takes it.
+template <int G, int CPL>
+__global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* scratch, WalkerLayout WL) {
+    extern __shared__ __align__(16) unsigned char smem[];
     const int lg = threadIdx.x & (G - 1);
     const unsigned gmask = group_mask<G>();
-    const int64_t walker = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    char* ws = scratch + walker * W.bytes();
-    const int Kmax = W.Kmax, dimPad = W.dimPad, S = Kmax + 1;
-    int32_t* lv_u = reinterpret_cast<int32_t*>(ws);
-    int32_t* lv_u1 = lv_u + Kmax;
-    int32_t* lv_zi = lv_u1 + Kmax;
-    int32_t* lv_meta = lv_zi + Kmax;
-    int32_t* lv_J = lv_meta + Kmax;
-    double* lv_y = reinterpret_cast<double*>(ws + ((int64_t)5 * Kmax * 4 + 15) / 16 * 16);
-    double* lv_rhoP = lv_y + Kmax;
-    double* wstack = lv_rhoP + Kmax;
-    double* sigma = wstack + (int64_t)Kmax * dimPad;
+    const int wib = threadIdx.x / G;
+    const int64_t walker = (int64_t)blockIdx.x * (blockDim.x / G) + wib;
+    const int Kmax = WL.Kmax, dimPad = WL.dimPad, S = Kmax + 1;
+    const Levels L = levels_at(smem + (int64_t)wib * level_bytes(Kmax), Kmax);
+    char* ws = scratch + walker * WL.bytes();
+    double* root_w = reinterpret_cast<double*>(ws);
+    double* sigma = root_w + dimPad;
     Ctrl* ctrl = P.ctrl;
 
     const int64_t total = P.qbase[P.count];
@@ -359,12 +569,6 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
         // ---- set up the walk ----
         int inst;
         int64_t gid;
-        int t0;
-        double w_par[CPL], w_ch[CPL];
-        double rhoP, y = 0.0;
-        int u = 0, u1 = 0, s = 1, zi = 1, dir = 0;
-        bool onedir = false, zp = true;
-        int act;
         if (src == 1) {
             gid = P.qperm ? P.qperm[id] : (int64_t)id;
             int lo = 0, hi = P.count;
@@ -379,13 +583,23 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
             gid = hd->gid;
         }
         const InstDesc& I = P.inst[inst];
-        const int dd = I.dd, dim = I.dim, n = I.n, m = I.m;
+        const int dd = I.dd, dim = I.dim;
+        const int sx = I.sx, Sf = I.sx + I.sb;
         const double* __restrict__ muT = P.muT + I.offMuT;
-        const double* __restrict__ Bt = P.B + I.offB;
+        const double* __restrict__ Btab = P.B + I.offB;
         const double* __restrict__ bhat = P.bhat + I.offBhat;
-        const int32_t* __restrict__ kb = P.kb + I.offKb;
+        const int32_t* __restrict__ bqtab = P.bq + I.offBq;
+        const int64_t* __restrict__ nbqtab = P.nbq + I.offNbq;
         const double eps = slack_of(dim, cfg.use_eps);
-        const double Rb = (double)dim + eps;
+        const long long Rbits = __double_as_longlong((double)dim + eps);
+        const long long eps_fix = (long long)dim << (Sf - 20);   // eps 2^(sx+sb), exact
+        const long long ehalf = dim;                              // (n+1)
+
+        int t0;
+        double y = 0.0, rhoP;
+        int u = 0, u1 = 0, s = 1, zi = 1, dir = 0;
+        bool onedir = false, zp = true;
+        int act;
         if (src == 1) {
             const int split_level = I.split_level;
             t0 = split_level - 1;
@@ -393,16 +607,12 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
             const int32_t* pu = P.fu + fo * P.Kmax;
             for (int i = split_level; i < dd; ++i) {
                 const int32_t v = pu[i];
-                lv_u[i] = v;
+                if (lg == 0) L.u[i] = (short)v;
                 zp = zp && (v == 0);
             }
-#pragma unroll
-            for (int q = 0; q < CPL; ++q) {
-                const int c = lg + G * q;
-                w_par[q] = (c < dim) ? P.fw[fo * P.dimPad + c] : 0.0;
-            }
+            for (int c = lg; c < dim; c += G) root_w[c] = P.fw[fo * P.dimPad + c];
             rhoP = P.frho[fo];
-            act = kEval;   // fresh level: enter it below
+            act = kEval;   // fresh level: entered below
         } else {
             const char* slot = P.don + id * P.don_stride;
             const DonHdr hd = *reinterpret_cast<const DonHdr*>(slot);
@@ -410,12 +620,8 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
             const double* sw = reinterpret_cast<const double*>(
                 slot + ((int64_t)sizeof(DonHdr) + (int64_t)Kmax * 4 + 15) / 16 * 16);
             t0 = hd.t;
-            for (int i = t0 + 1; i < dd; ++i) lv_u[i] = su[i];
-#pragma unroll
-            for (int q = 0; q < CPL; ++q) {
-                const int c = lg + G * q;
-                w_par[q] = (c < dim) ? sw[c] : 0.0;
-            }
+            for (int i = t0 + 1 + lg; i < dd; i += G) L.u[i] = (short)su[i];
+            for (int c = lg; c < dim; c += G) root_w[c] = sw[c];
             rhoP = hd.rhoP;
             y = hd.y;
             u = hd.u;
@@ -426,34 +632,41 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
             if (onedir) dir = hd.zi; else zi = hd.zi;
             act = kNext;   // the donor evaluated u already
         }
-        for (int i = lg; i <= t0; i += G) lv_J[i] = dd - 1;
+        for (int i = lg; i <= t0; i += G) L.J[i] = (unsigned char)(dd - 1);
         for (int i = lg; i < dd; i += G) sigma[(int64_t)i * S + dd] = 0.0;
+        if (lg == 0) L.meta[t0] = 0;
+        __syncwarp(gmask);
+        // integer root vector, error bound, and the table row of level t0
+        long long W[CPL];
+        int bq[CPL];
 #pragma unroll
         for (int q = 0; q < CPL; ++q) {
             const int c = lg + G * q;
-            w_ch[q] = 0.0;
-            if (c < dim) wstack[(int64_t)t0 * dimPad + c] = w_par[q];
+            W[q] = (c < dim) ? llrint(ldexp(root_w[c], Sf)) : 0LL;
         }
-        if (lg == 0) lv_meta[t0] = 0;
-        __syncwarp(gmask);
-
-        unsigned long long nodes = 0, passed = 0, leaves = 0, cfma = 0;
-        int item_sols = 0;
+        long long Epar = ehalf;
         int t = t0;
+        double Bt = Btab[t];
+        long long nbq_t = nbqtab[t];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) bq[q] = bqtab[(int64_t)t * dimPad + lg + G * q];
+
+        unsigned long long nodes = 0, passed = 0, leaves = 0, cfma = 0, fallbacks = 0;
+        int item_sols = 0;
         bool abort = false;
 
         // entering level t: centre by the cached fold, start of the zig-zag
         auto enter_level = [&]() {
-            const int Jt = lv_J[t];
+            const int Jt = L.J[t];
             double acc = sigma[(int64_t)t * S + Jt + 1];
             for (int i = Jt; i > t; --i) {
-                acc = __fma_rn((double)lv_u[i], muT[(int64_t)t * dd + i], acc);
+                acc = __fma_rn(i2d_exact(L.u[i]), muT[(int64_t)t * dd + i], acc);
                 sigma[(int64_t)t * S + i] = acc;
             }
             y = acc;
             cfma += (unsigned long long)(Jt - t);
-            if (t > 0) lv_J[t - 1] = max(lv_J[t - 1], Jt);
-            lv_J[t] = t;
+            if (t > 0 && L.J[t - 1] < Jt) L.J[t - 1] = (unsigned char)Jt;
+            L.J[t] = (unsigned char)t;
             const double cstar = -y;
             const double r1 = rint(cstar);
             if (fabs(r1) >= (double)kUMax) abort = true;
@@ -462,15 +675,15 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
             onedir = false; dir = 0; zi = 1;
             if (zp && cfg.sym) { u1 = 0; onedir = true; dir = 1; }
             u = u1;
-            if (t > 0) lv_J[t - 1] = max(lv_J[t - 1], t);
+            if (t > 0 && L.J[t - 1] < t) L.J[t - 1] = (unsigned char)t;
         };
-        if (src == 1) enter_level();
+        if (src == 1) { __syncwarp(gmask); enter_level(); }
 
         while (!abort) {
             if (act == kNext) {
                 if (onedir) u += dir;
                 else { ++zi; u = zigzag(u1, s, zi); }
-                if (t > 0) lv_J[t - 1] = max(lv_J[t - 1], t);
+                if (t > 0 && L.J[t - 1] < t) L.J[t - 1] = (unsigned char)t;
             }
             if ((nodes & 1023) == 1023) {
                 // stop flag, time cap, and donation to idle walkers
@@ -483,141 +696,55 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
                     }
                     const int idle = *(volatile int*)&ctrl->idle;
                     if (idle > 0) {
-                        const unsigned long long q = *(volatile unsigned long long*)&ctrl->dtail -
-                                                     *(volatile unsigned long long*)&ctrl->dhead;
-                        want = q < (unsigned long long)idle;
+                        const unsigned long long qd = *(volatile unsigned long long*)&ctrl->dtail -
+                                                      *(volatile unsigned long long*)&ctrl->dhead;
+                        want = qd < (unsigned long long)idle;
                     }
                 }
                 if (__shfl_sync(gmask, st, 0, G)) { abort = true; break; }
-                if (__shfl_sync(gmask, want, 0, G)) {
-                    int h = -1;
-                    for (int l = t0; l > t; --l)
-                        if (!(lv_meta[l] & kDonated)) { h = l; break; }
-                    if (h >= 0) {
-                        long long slot = -1;
-                        if (lg == 0) {
-                            for (int tries = 0; tries < 64; ++tries) {
-                                const unsigned long long old = *(volatile unsigned long long*)&ctrl->dtail;
-                                if ((int64_t)old >= P.don_cap) break;
-                                if (atomicCAS(&ctrl->dtail, old, old + 1) == old) { slot = (long long)old; break; }
-                            }
-                        }
-                        slot = __shfl_sync(gmask, slot, 0, G);
-                        if (slot >= 0) {
-                            char* sp = P.don + slot * P.don_stride;
-                            int32_t* su = reinterpret_cast<int32_t*>(sp + sizeof(DonHdr));
-                            double* sw = reinterpret_cast<double*>(
-                                sp + ((int64_t)sizeof(DonHdr) + (int64_t)Kmax * 4 + 15) / 16 * 16);
-                            if (lg == 0) {
-                                DonHdr hd;
-                                hd.inst = inst; hd.t = h; hd.u = lv_u[h]; hd.u1 = lv_u1[h];
-                                hd.zi = lv_zi[h]; hd.meta = lv_meta[h] & ~kDonated; hd.gid = gid;
-                                hd.y = lv_y[h]; hd.rhoP = lv_rhoP[h];
-                                *reinterpret_cast<DonHdr*>(sp) = hd;
-                            }
-                            for (int i = h + 1 + lg; i < dd; i += G) su[i] = lv_u[i];
-                            for (int c = lg; c < dim; c += G) sw[c] = wstack[(int64_t)h * dimPad + c];
-                            __threadfence();
-                            __syncwarp(gmask);
-                            if (lg == 0) atomicExch(&P.don_ready[slot], 1u);
-                            lv_meta[h] |= kDonated;
-                            __syncwarp(gmask);
-                        }
-                    }
-                }
+                if (__shfl_sync(gmask, want, 0, G))
+                    donate<G>(P, inst, gid, L, root_w, bhat, t0, t, dd, dim, Kmax, gmask);
             }
             if (u >= kUMax || u <= -kUMax) { abort = true; set_status(const_cast<InstDesc&>(I), ST_EOVERFLOW); break; }
-            const double x = __dadd_rn((double)u, y);
-            const double rho = __fma_rn(__dmul_rn(x, x), Bt[t], rhoP);
+            // ---- node (t, u): centre, norm (FP64, the canonical operations) ----
+            const double x = __dadd_rn(i2d_exact(u), y);
+            const double rho = __fma_rn(__dmul_rn(x, x), Bt, rhoP);
             ++nodes;
-            if (!(rho <= Rb)) {   // norm test (a NaN never passes)
+            long long T[CPL];
+            long long Ech = 0;
+            int xq = 0;
+            if (__double_as_longlong(rho) > Rbits) {   // norm test on the bit patterns (rho >= 0)
                 act = kUp;
             } else {
                 ++passed;
                 if (t == 0) {
                     ++leaves;
-                    // exact Theorem 1 check of v = sum_j u_j b_j
-                    long long v[CPL];
-#pragma unroll
-                    for (int q = 0; q < CPL; ++q) {
-                        const int c = lg + G * q;
-                        long long a = 0;
-                        if (c < dim) {
-                            a = (long long)u * kb[c];
-                            for (int j = 1; j < dd; ++j) a += (long long)lv_u[j] * kb[(int64_t)j * dim + c];
-                        }
-                        v[q] = a;
-                    }
-                    long long mine = 0;
-#pragma unroll
-                    for (int q = 0; q < CPL; ++q) if (q == (dim - 1) / G) mine = v[q];
-                    const long long last = __shfl_sync(gmask, mine, (dim - 1) % G, G);
-                    const long long sg = (cfg.sym && last == -1) ? -1 : 1;
-                    bool ok = (last * sg == 1);
-                    unsigned long long khi = 0, klo = 0;
-#pragma unroll
-                    for (int q = 0; q < CPL; ++q) {
-                        const int c = lg + G * q;
-                        const long long vc = v[q] * sg;
-                        if (c < n && vc != 1 && vc != -1) ok = false;
-                    }
-                    ok = __all_sync(gmask, ok);
-                    if (ok) {
-                        const int gi = (threadIdx.x & 31) / G;
-#pragma unroll
-                        for (int q = 0; q < CPL; ++q) {
-                            const int c = lg + G * q;
-                            const bool one = (c < n) && (v[q] * sg == 1);
-                            unsigned bits = __ballot_sync(gmask, one) >> (gi * G);
-                            if (G < 32) bits &= (1u << (G & 31)) - 1u;
-                            for (int l = 0; l < G; ++l) {
-                                if ((bits >> l) & 1u) {
-                                    const int cc = G * q + l;   // x_cc = 1 at key bit 127 - cc
-                                    if (cc < 64) khi |= 1ULL << (63 - cc);
-                                    else klo |= 1ULL << (127 - cc);
-                                }
-                            }
-                        }
-                        // independent verification A x = d
-                        const int32_t* Ai = P.A + I.offA;
-                        const int64_t* di = P.d + I.offd;
-                        for (int i = lg; i < m; i += G) {
-                            long long acc = 0;
-                            for (int c = 0; c < n; ++c) {
-                                const bool xc = c < 64 ? (khi >> (63 - c)) & 1ULL : (klo >> (127 - c)) & 1ULL;
-                                if (xc) acc += Ai[(int64_t)i * n + c];
-                            }
-                            if (acc != di[i]) ok = false;
-                        }
-                        ok = __all_sync(gmask, ok);
-                        if (ok && lg == 0) {
-                            const unsigned long long k = atomicAdd(&ctrl->nsol_total, 1ULL);
-                            if ((int64_t)k < P.sol_cap) {
-                                SolRec r;
-                                r.inst = inst; r.pad = 0; r.hi = khi; r.lo = klo;
-                                P.sols[k] = r;
-                            }
-                            atomicAdd(&P.cnt[inst].nsol, 1ULL);
-                            if (cfg.first) atomicExch(&ctrl->stop, 1u);
-                        }
-                        if (ok) ++item_sols;
-                    }
+                    item_sols += leaf_check<G, CPL>(P, cfg, inst, L, u, gmask);
                     act = kNext;
                 } else {
-                    double sl = 0.0;
+                    // ---- Hoelder test (Theorem 2) through the exact integer filter ----
+                    xq = (int)fix_trunc(x, sx);
+                    long long lsum = 0;
 #pragma unroll
                     for (int q = 0; q < CPL; ++q) {
-                        const int c = lg + G * q;
-                        if (c < dim) {
-                            w_ch[q] = __fma_rn(x, bhat[(int64_t)t * dim + c], w_par[q]);
-                            sl = __dadd_rn(sl, fabs(w_ch[q]));
-                        }
+                        T[q] = W[q] + (long long)xq * (long long)bq[q];
+                        lsum += T[q] < 0 ? -T[q] : T[q];
                     }
 #pragma unroll
-                    for (int off = G / 2; off >= 1; off >>= 1)
-                        sl = __dadd_rn(sl, __shfl_xor_sync(gmask, sl, off, G));
+                    for (int off = G / 2; off >= 1; off >>= 1) lsum += __shfl_xor_sync(gmask, lsum, off, G);
+                    const long long axq = xq < 0 ? -(long long)xq : (long long)xq;
+                    Ech = Epar + ((ehalf * (axq + 1)) >> 1) + nbq_t + 1;
                     bool fail = false;
-                    if (cfg.hoelder != HOELDER_OFF) fail = rho > __dadd_rn(sl, eps);
+                    if (cfg.hoelder != HOELDER_OFF) {
+                        const long long M = fix_trunc(rho, Sf) - lsum - eps_fix;
+                        const long long Etot = Ech + (Ech >> 10) + (lsum >> 32) + 64;
+                        if (M > Etot) fail = true;
+                        else if (M < -Etot) fail = false;
+                        else {
+                            ++fallbacks;
+                            fail = rho > __dadd_rn(canonical_l1<G, CPL>(bhat, root_w, L, t0, t, x, dim, gmask), eps);
+                        }
+                    }
                     if (fail && cfg.hoelder == HOELDER_CUT) {
                         if (onedir) {
                             act = kUp;
@@ -627,7 +754,7 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
                             u = zigzag(u1, s, zi);
                             dir = (u > u1) ? 1 : -1;
                             onedir = true;
-                            lv_J[t - 1] = max(lv_J[t - 1], t);
+                            if (L.J[t - 1] < t) L.J[t - 1] = (unsigned char)t;
                             act = kEval;
                         }
                     } else {
@@ -636,51 +763,59 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
                 }
             }
             if (act == kDescend) {
-                // save level t, make the child the parent of level t-1
-                lv_u[t] = u;
-                lv_u1[t] = u1;
-                lv_zi[t] = onedir ? dir : zi;
-                lv_meta[t] = (onedir ? kOneDir : 0) | (s < 0 ? kNegS : 0) | (zp ? kZeroPrefix : 0);
-                lv_y[t] = y;
-                lv_rhoP[t] = rhoP;
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) {
-                    const int c = lg + G * q;
-                    w_par[q] = w_ch[q];
-                    if (c < dim) wstack[(int64_t)(t - 1) * dimPad + c] = w_ch[q];
+                // save level t; the child becomes the parent of level t-1
+                if (lg == 0) {
+                    L.u[t] = (short)u;
+                    L.u1[t] = (short)u1;
+                    L.zi[t] = (short)(onedir ? dir : zi);
+                    L.meta[t] = (unsigned char)((onedir ? kOneDir : 0) | (s < 0 ? kNegS : 0) | (zp ? kZeroPrefix : 0));
+                    L.xq[t] = xq;
+                    L.y[t] = y;
+                    L.rho[t] = rhoP;
                 }
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) W[q] = T[q];
+                Epar = Ech;
                 rhoP = rho;
                 zp = zp && (u == 0);
                 --t;
+                Bt = Btab[t];
+                nbq_t = nbqtab[t];
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) bq[q] = bqtab[(int64_t)t * dimPad + lg + G * q];
                 __syncwarp(gmask);
                 enter_level();
                 act = kEval;
                 continue;
             }
             if (act == kUp) {
-                // step back; levels whose remaining values were donated are done
+                // step back; subtract each level's term; donated levels are done
                 bool done = false;
                 int meta = 0;
                 do {
                     if (t == t0) { done = true; break; }
                     ++t;
-                    meta = lv_meta[t];
+                    meta = L.meta[t];
+                    const int xqt = L.xq[t];
+                    const long long axt = xqt < 0 ? -(long long)xqt : (long long)xqt;
+                    nbq_t = nbqtab[t];
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) {
+                        bq[q] = bqtab[(int64_t)t * dimPad + lg + G * q];
+                        W[q] -= (long long)xqt * (long long)bq[q];
+                    }
+                    Epar -= ((ehalf * (axt + 1)) >> 1) + nbq_t + 1;
                 } while (meta & kDonated);
                 if (done) break;
-                u = lv_u[t];
-                u1 = lv_u1[t];
+                u = L.u[t];
+                u1 = L.u1[t];
                 onedir = meta & kOneDir;
                 s = (meta & kNegS) ? -1 : 1;
                 zp = (meta & kZeroPrefix) != 0;
-                if (onedir) dir = lv_zi[t]; else zi = lv_zi[t];
-                y = lv_y[t];
-                rhoP = lv_rhoP[t];
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) {
-                    const int c = lg + G * q;
-                    w_par[q] = (c < dim) ? wstack[(int64_t)t * dimPad + c] : 0.0;
-                }
-                __syncwarp(gmask);
+                if (onedir) dir = L.zi[t]; else zi = L.zi[t];
+                y = L.y[t];
+                rhoP = L.rho[t];
+                Bt = Btab[t];
                 act = kNext;
             }
         }
@@ -690,6 +825,7 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
             atomicAdd(&P.cnt[inst].passed, passed);
             atomicAdd(&P.cnt[inst].leaves, leaves);
             atomicAdd(&P.cnt[inst].center_fma, cfma);
+            atomicAdd(&P.cnt[inst].fallbacks, fallbacks);
             atomicAdd(reinterpret_cast<unsigned long long*>(&P.plog_nodes[gid]), nodes);
             if (item_sols) atomicAdd(&P.plog_sols[gid], item_sols);
             atomicSub(&ctrl->busy, 1);
@@ -751,9 +887,28 @@ __global__ void sol_rank_kernel(Pools P, const int64_t* soff, const SolRec* seg,
 // ---------------------------------------------------------------------------
 // Host-side launch helpers (called from api.cu).
 // ---------------------------------------------------------------------------
+// (G, CPL) instances: CPL = coordinates per lane, G * CPL >= n + 1
+#define MSP_ENUM_SHAPES(X) X(4, 16) X(4, 32) X(8, 8) X(8, 16) X(16, 4) X(16, 8) X(32, 4)
+
+static int pick_cpl(int lanes, int dimMax) {
+    const int need = (dimMax + lanes - 1) / lanes;
+    const int opts[] = {4, 8, 16, 32};
+    for (int c : opts) {
+        if (c < need) continue;
+        switch (lanes * 100 + c) {
+            case 416: case 432: case 808: case 816: case 1604: case 1608: case 3204: return c;
+            default: break;
+        }
+    }
+    return 0;
+}
+
+int enum_smem_bytes(int lanes, int threads, int Kmax) { return (threads / lanes) * level_bytes(Kmax); }
+
 cudaError_t launch_split(const Pools& P, const EnumCfg& cfg, int lanes, int max_depth, int64_t target,
                          int64_t* fcnt, cudaStream_t st) {
     switch (lanes) {
+        case 4: split_kernel<4><<<P.count, 256, 0, st>>>(P, cfg, max_depth, target, fcnt); break;
         case 8: split_kernel<8><<<P.count, 256, 0, st>>>(P, cfg, max_depth, target, fcnt); break;
         case 16: split_kernel<16><<<P.count, 256, 0, st>>>(P, cfg, max_depth, target, fcnt); break;
         case 32: split_kernel<32><<<P.count, 256, 0, st>>>(P, cfg, max_depth, target, fcnt); break;
@@ -770,14 +925,17 @@ cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, cudaStream_t st)
     return cudaGetLastError();
 }
 
-int enum_blocks_per_sm(int lanes, int threads) {
+int enum_blocks_per_sm(int lanes, int threads, int dimMax, int Kmax) {
     int n = 0;
-    switch (lanes) {
-        case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<8>, threads, 0); break;
-        case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<16>, threads, 0); break;
-        case 32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<32>, threads, 0); break;
-        default: break;
+    const int cpl = pick_cpl(lanes, dimMax);
+    const int smem = enum_smem_bytes(lanes, threads, Kmax);
+#define MSP_OCC(g, c)                                                                                 \
+    if (lanes == g && cpl == c) {                                                                     \
+        cudaFuncSetAttribute(enum_kernel<g, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);   \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<g, c>, threads, smem);          \
     }
+    MSP_ENUM_SHAPES(MSP_OCC)
+#undef MSP_OCC
     return n;
 }
 
@@ -788,13 +946,17 @@ int64_t donation_slot_bytes(int Kmax, int dimPad) { return donation_stride(Kmax,
 cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
                         int Kmax, int dimPad, cudaStream_t st) {
     WalkerLayout W{Kmax, dimPad};
-    switch (lanes) {
-        case 8: enum_kernel<8><<<blocks, threads, 0, st>>>(P, cfg, scratch, W); break;
-        case 16: enum_kernel<16><<<blocks, threads, 0, st>>>(P, cfg, scratch, W); break;
-        case 32: enum_kernel<32><<<blocks, threads, 0, st>>>(P, cfg, scratch, W); break;
-        default: return cudaErrorInvalidValue;
+    const int cpl = pick_cpl(lanes, P.dimMax);
+    const int smem = enum_smem_bytes(lanes, threads, Kmax);
+#define MSP_LAUNCH(g, c)                                                                              \
+    if (lanes == g && cpl == c) {                                                                     \
+        cudaFuncSetAttribute(enum_kernel<g, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);   \
+        enum_kernel<g, c><<<blocks, threads, smem, st>>>(P, cfg, scratch, W);                         \
+        return cudaGetLastError();                                                                    \
     }
-    return cudaGetLastError();
+    MSP_ENUM_SHAPES(MSP_LAUNCH)
+#undef MSP_LAUNCH
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_collect(const Pools& P, int64_t* soff, unsigned long long* fill, SolRec* seg, SolRec* out,

@@ -332,4 +332,49 @@ __global__ void __launch_bounds__(32) extract_gso_kernel(Pools P) {
     if (lane == 0) { I.dd = dd; I.dim = dim; }
 }
 
+// Fixed-point parameters of the exact integer filter used by the walkers
+// for the Hoelder test (one warp per instance, after extract_gso_kernel):
+//   sx: |x| <= sqrt((R + eps) / B_t) on every node that passes the norm test,
+//       so trunc(x 2^sx) fits in 31 bits;
+//   sb: |bhat_tc| <= sqrt(B_t), so round(bhat 2^sb) fits in 31 bits;
+//   sx + sb <= 50 keeps |w|_1 2^(sx+sb) <= sqrt(n+1) |w|_2 2^50 inside int64.
+__global__ void __launch_bounds__(32) prep_fixed_kernel(Pools P, int use_eps, int dimPad) {
+    InstDesc& I = P.inst[blockIdx.x];
+    const int lane = threadIdx.x;
+    if (I.status != ST_OK) return;
+    const int dd = I.dd, dim = I.dim;
+    const double* Bt = P.B + I.offB;
+    const double* bhat = P.bhat + I.offBhat;
+    const double Rb = (double)dim + (use_eps ? (double)dim * 0x1p-20 : 0.0);
+    double xm = 0.0, bm = 0.0;
+    for (int t = lane; t < dd; t += 32) xm = fmax(xm, sqrt(Rb / Bt[t]));
+    for (int e = lane; e < dd * dim; e += 32) bm = fmax(bm, fabs(bhat[e]));
+    for (int off = 16; off >= 1; off >>= 1) {
+        xm = fmax(xm, __shfl_xor_sync(kFull, xm, off));
+        bm = fmax(bm, __shfl_xor_sync(kFull, bm, off));
+    }
+    int ex, eb;
+    frexp(xm * 1.0001 + 1.0, &ex);   // xm < 2^ex
+    frexp(bm * 1.0001 + 1.0, &eb);
+    const int sx = min(25, 30 - ex), sb = min(25, 30 - eb);
+    if (sx < 8 || sb < 8) {          // values too large for a useful filter
+        if (lane == 0) set_status(I, ST_EOVERFLOW);
+        return;
+    }
+    int32_t* bq = P.bq + I.offBq;
+    int64_t* nbq = P.nbq + I.offNbq;
+    const double scale = ldexp(1.0, sb);
+    for (int t = 0; t < dd; ++t) {
+        long long s = 0;
+        for (int c = lane; c < dimPad; c += 32) {
+            const int v = (c < dim) ? __double2int_rn(bhat[(int64_t)t * dim + c] * scale) : 0;
+            bq[(int64_t)t * dimPad + c] = v;
+            s += (v < 0) ? -(long long)v : (long long)v;
+        }
+        for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+        if (lane == 0) nbq[t] = s;
+    }
+    if (lane == 0) { I.sx = sx; I.sb = sb; }
+}
+
 }  // namespace msp
