@@ -83,8 +83,8 @@ typedef struct {
     int64_t sol_capacity;  /* [1<<20] solutions stored (over all instances)               */
     double max_seconds;    /* [600] safety cap on every enumeration's device time; the     */
                            /*       walkers stop and report MSP_ETIMEOUT when it passes   */
-    int64_t donation_capacity; /* [1<<18] sibling ranges busy walkers may hand to idle */
-                           /*       ones during one enumeration (0: no donation)          */
+    int64_t donation_capacity; /* [1<<16] slots of the ring through which busy walkers */
+                           /*       hand sibling ranges to idle ones (0: no donation)      */
 } msp_opts;
 
 /* Per-instance results of an enumeration. */
@@ -104,6 +104,8 @@ typedef struct {
     int64_t center_fma;    /* fmas spent by the walkers on the centres y_t            */
     int64_t fallbacks;     /* Hoelder tests too close to call from the exact integer  */
                            /* filter, decided by rebuilding the FP64 vector           */
+    int64_t donations;     /* batch total only: sibling ranges handed between walkers */
+    double walker_util;    /* batch total only: fraction of walker time spent walking */
     int32_t status;        /* msp_status of this instance                              */
     int32_t reserved;
     double ms;             /* wall time of the enumeration call (whole batch)          */

@@ -107,23 +107,25 @@ static int dot_exact(const int64_t *a, const int64_t *b, int L, int64_t *out)
 }
 
 /* Gram-Schmidt row k from the exact Gram matrix G (K x K, full):
- *   r_kj = G_kj - sum_{i<j} mu_ji r_ki,  mu_kj = r_kj / r_jj,
- *   r_kk = G_kk - sum_{i<k} mu_ki r_ki,  B_k = r_kk.
- * This is Eq. (4) written with r_kj = <b_k, bhat_j>. */
-static void gso_row(int k, int K, const int64_t *G, double *mu, double *r, double *B)
+ *   r_kj = G_kj - sum_{i<j} mu_ji r_ki,  mu_kj = r_kj * (1 / r_jj),
+ *   r_kk = G_kk - sum_{i<k} mu_ki r_ki,  B_k = r_kk,  invB_k = 1 / B_k.
+ * This is Eq. (4) written with r_kj = <b_k, bhat_j>; inside the reduction
+ * mu is formed with the reciprocal of B_j, computed once per row. */
+static void gso_row(int k, int K, const int64_t *G, double *mu, double *r, double *B, double *invB)
 {
     for (int j = 0; j < k; ++j) {
         double acc = (double)G[(size_t)k * K + j];
         for (int i = 0; i < j; ++i)
             acc = fma(-mu[(size_t)j * K + i], r[(size_t)k * K + i], acc);
         r[(size_t)k * K + j] = acc;
-        mu[(size_t)k * K + j] = acc / B[j];
+        mu[(size_t)k * K + j] = acc * invB[j];
     }
     double acc = (double)G[(size_t)k * K + k];
     for (int i = 0; i < k; ++i)
         acc = fma(-mu[(size_t)k * K + i], r[(size_t)k * K + i], acc);
     r[(size_t)k * K + k] = acc;
     B[k] = acc;
+    invB[k] = 1.0 / acc;
 }
 
 static int gram_row(int k, int K, int L, const int64_t *b, int64_t *G)
@@ -148,12 +150,13 @@ int oracle_lll(int K, int L, int64_t *b, double delta, double eta, int64_t max_i
     double *mu = (double *)calloc((size_t)K * K, sizeof(double));
     double *r = (double *)calloc((size_t)K * K, sizeof(double));
     double *B = (double *)calloc((size_t)K, sizeof(double));
+    double *invB = (double *)calloc((size_t)K, sizeof(double));
     int64_t iters = 0, swaps = 0;
-    if (!G || !mu || !r || !B) { st = OR_ENOMEM; goto done; }
+    if (!G || !mu || !r || !B || !invB) { st = OR_ENOMEM; goto done; }
 
     for (int k = 0; k < K; ++k)
         if ((st = gram_row(k, K, L, b, G))) goto done;
-    gso_row(0, K, G, mu, r, B);
+    gso_row(0, K, G, mu, r, B, invB);
 
     int k = 1;
     while (k < K) {
@@ -161,7 +164,7 @@ int oracle_lll(int K, int L, int64_t *b, double delta, double eta, int64_t max_i
         /* lazy size reduction: reduce, recompute the row exactly, repeat */
         for (int pass = 0;; ++pass) {
             if (pass > 1000) { st = OR_ECAP; goto done; }
-            gso_row(k, K, G, mu, r, B);
+            gso_row(k, K, G, mu, r, B, invB);
             int changed = 0;
             for (int j = k - 1; j >= 0; --j) {
                 double mkj = mu[(size_t)k * K + j];
@@ -204,7 +207,7 @@ int oracle_lll(int K, int L, int64_t *b, double delta, double eta, int64_t max_i
                 G[(size_t)i * K + (k - 1)] = t;
             }
             ++swaps;
-            if (k - 1 == 0) gso_row(0, K, G, mu, r, B);
+            if (k - 1 == 0) gso_row(0, K, G, mu, r, B, invB);
             k = (k > 1) ? k - 1 : 1;
         } else {
             ++k;
@@ -213,7 +216,7 @@ int oracle_lll(int K, int L, int64_t *b, double delta, double eta, int64_t max_i
 done:
     if (iters_out) *iters_out = iters;
     if (swaps_out) *swaps_out = swaps;
-    free(G); free(mu); free(r); free(B);
+    free(G); free(mu); free(r); free(B); free(invB);
     return st;
 }
 

@@ -26,6 +26,7 @@ cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int block
 cudaError_t launch_collect(const Pools& P, int64_t* soff, unsigned long long* fill, SolRec* seg, SolRec* out,
                            cudaStream_t st);
 cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, cudaStream_t st);
+cudaError_t launch_ring_init(unsigned long long* seq, int64_t cap, cudaStream_t st);
 int64_t walker_bytes(int Kmax, int dimPad);
 int64_t donation_slot_bytes(int Kmax, int dimPad);
 int enum_blocks_per_sm(int lanes, int threads, int dimMax, int Kmax);
@@ -47,7 +48,7 @@ struct Buf {
 struct msp_ctx {
     msp_opts o;
     cudaStream_t st = nullptr;
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, smem_optin = 48 * 1024;
     std::string err;
     int64_t launches = 0;
     int state = 0;   // 0 empty, 1 lattice built, 2 reduced, 3 enumerated
@@ -65,7 +66,7 @@ struct msp_ctx {
     bool reduce_timed = false;
     // device buffers
     Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, bq, nbq, fu, frho, fw, fcnt, qbase, sols, ctrl, soff,
-        fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_ready;
+        fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_seq;
     std::vector<int64_t> soff_h;
     std::vector<SolRec> sout_h;
     bool sout_valid = false;
@@ -136,7 +137,7 @@ void refresh_pools(msp_ctx* c) {
     P.plog_nodes = ptr<int64_t>(c->plog_nodes);
     P.plog_sols = ptr<int32_t>(c->plog_sols);
     P.don = ptr<char>(c->don);
-    P.don_ready = ptr<unsigned int>(c->don_ready);
+    P.don_seq = ptr<unsigned long long>(c->don_seq);
     P.don_cap = c->o.donation_capacity;
     P.don_stride = donation_slot_bytes(c->Kmax, c->dimPad);
     P.sols = ptr<SolRec>(c->sols);
@@ -146,10 +147,14 @@ void refresh_pools(msp_ctx* c) {
 
 int walkers_of(const msp_ctx* c, int blocks, int threads) { return blocks * threads / c->o.lanes; }
 
+// Threads per enumeration block: the requested warps, reduced while the
+// walkers' level state would not fit the shared memory a block may use.
 void enum_launch_shape(const msp_ctx* c, int* blocks, int* threads) {
-    *threads = c->o.warps_per_block * 32;
+    int t = c->o.warps_per_block * 32;
+    while (t > 32 && enum_smem_bytes(c->o.lanes, t, c->Kmax) > c->smem_optin) t -= 32;
+    *threads = t;
     int bps = c->o.blocks_per_sm;
-    if (bps <= 0) bps = std::max(1, enum_blocks_per_sm(c->o.lanes, *threads, c->dimMax, c->Kmax));
+    if (bps <= 0) bps = std::max(1, enum_blocks_per_sm(c->o.lanes, t, c->dimMax, c->Kmax));
     *blocks = c->sms * bps;
 }
 
@@ -182,7 +187,7 @@ void msp_default_opts(msp_opts* o) {
     o->smem_tables = 1;
     o->sol_capacity = 1 << 20;
     o->max_seconds = 600.0;
-    o->donation_capacity = 1 << 18;
+    o->donation_capacity = 1 << 16;
 }
 
 const char* msp_status_string(int s) {
@@ -223,6 +228,7 @@ msp_status msp_create(msp_ctx** out, const msp_opts* opts, void* stream) {
     c->st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaGetDevice(&c->dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
     if (e == cudaSuccess) e = cudaEventCreate(&c->evr0);
@@ -244,7 +250,7 @@ void msp_destroy(msp_ctx* c) {
     Buf* all[] = {&c->inst, &c->cnt, &c->A, &c->d, &c->basis, &c->gram, &c->mu, &c->Bl, &c->kb, &c->muT, &c->B,
                   &c->bhat, &c->bq, &c->nbq, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
                   &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols, &c->don,
-                  &c->don_ready};
+                  &c->don_seq};
     for (Buf* b : all)
         if (b->p) cudaFree(b->p);
     for (cudaEvent_t ev : {c->ev0, c->ev1, c->evr0, c->evr1, c->evs1, c->eve1})
@@ -271,7 +277,7 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
         I.offd = nd; nd += m;
         I.offBasis = nBasis; nBasis += (int64_t)I.K * I.L;
         I.offGram = nGram; nGram += (int64_t)I.K * I.K;
-        I.offMu = nMu; nMu += (int64_t)2 * I.K * I.K;
+        I.offMu = nMu; nMu += (int64_t)2 * I.K * I.K + I.K;
         I.offBl = nK; I.offB = nK; nK += I.K;
         I.offKb = nKb; I.offBhat = nKb; nKb += (int64_t)I.K * I.dim;
         I.offMuT = nT; nT += (int64_t)I.K * I.K;
@@ -318,7 +324,7 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     ENSURE(plog_nodes, sizeof(int64_t) * (size_t)count * c->F);
     ENSURE(plog_sols, sizeof(int32_t) * (size_t)count * c->F);
     ENSURE(don, (size_t)c->o.donation_capacity * donation_slot_bytes(Kmax, c->dimPad));
-    ENSURE(don_ready, sizeof(unsigned int) * (size_t)c->o.donation_capacity);
+    ENSURE(don_seq, sizeof(unsigned long long) * (size_t)std::max<int64_t>(c->o.donation_capacity, 1));
     ENSURE(qbase, sizeof(int64_t) * (count + 1));
     ENSURE(sols, sizeof(SolRec) * (size_t)c->o.sol_capacity);
     ENSURE(ctrl, sizeof(Ctrl));
@@ -378,7 +384,7 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
     cudaError_t e = cudaMemsetAsync(c->cnt.p, 0, sizeof(InstCounters) * c->count, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->plog_nodes.p, 0, c->plog_nodes.bytes, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->plog_sols.p, 0, c->plog_sols.bytes, c->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->don_ready.p, 0, c->don_ready.bytes, c->st);
+    if (e == cudaSuccess && c->o.donation_capacity > 0) e = launch_ring_init(ptr<unsigned long long>(c->don_seq), c->o.donation_capacity, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset counters");
     // the caller's cap, else the context's safety cap: no walk outlives it
     const double cap_s = time_cap_s > 0 ? std::min(time_cap_s, c->o.max_seconds) : c->o.max_seconds;
@@ -474,6 +480,8 @@ msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {
     }
     tot.status = first_bad;
     tot.ms = ms;
+    tot.donations = (int64_t)ctl.donations;
+    tot.walker_util = ctl.life_cycles ? (double)ctl.walk_cycles / (double)ctl.life_cycles : 0.0;
     if (stats) std::memcpy(stats, c->stats.data(), sizeof(msp_stats) * c->count);
     if (total) *total = tot;
     return first_bad;

@@ -30,7 +30,7 @@ struct InstDesc {
     int64_t offA, offd;      // A (int32, m*n), d (int64, m)
     int64_t offBasis;        // K*L int64   LLL basis, vector-major
     int64_t offGram;         // K*K int64   exact Gram matrix
-    int64_t offMu;           // 2*K*K f64   LLL mu and r
+    int64_t offMu;           // 2*K*K+K f64 LLL mu, r and 1/B
     int64_t offBl;           // K f64       LLL ||bhat||^2
     int64_t offKb;           // K*dim int32 kept (kernel) basis
     int64_t offMuT;          // K*K f64     muT[t][i] = mu[i][t]
@@ -87,7 +87,7 @@ struct Pools {
     int32_t* plog_sols;                // per prefix: solutions found in its subtree
     // donated sibling ranges (work handed from busy walkers to idle ones)
     char* don;                         // don_cap slots of don_stride bytes
-    unsigned int* don_ready;           // per slot: 1 once written
+    unsigned long long* don_seq;       // per slot sequence number (bounded MPMC ring)
     int64_t don_cap, don_stride;
     // solutions
     SolRec* sols;
@@ -101,6 +101,9 @@ struct Ctrl {
     unsigned long long dhead, dtail;   // donation queue: next to take / next free slot
     int idle;                          // walkers waiting for donated work
     int busy;                          // walkers holding work
+    unsigned long long donations;      // sibling ranges handed over
+    unsigned long long walk_cycles;    // sum over walkers of clock cycles spent walking
+    unsigned long long life_cycles;    // sum over walkers of clock cycles alive
     unsigned long long nsol_total;     // solutions found (all instances)
     unsigned long long deadline_ns;    // globaltimer deadline, 0 = none
     unsigned int stop;                 // 1: first solution found, 2: time cap

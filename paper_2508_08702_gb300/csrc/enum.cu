@@ -222,6 +222,9 @@ __global__ void start_kernel(Ctrl* c, unsigned long long cap_ns) {
     c->dtail = 0;
     c->idle = 0;
     c->busy = 0;
+    c->donations = 0;
+    c->walk_cycles = 0;
+    c->life_cycles = 0;
     c->nsol_total = 0;
     c->stop = 0;
     c->gstatus = 0;
@@ -244,7 +247,8 @@ __global__ void queue_kernel(Pools P) {
 // ---------------------------------------------------------------------------
 
 // Global scratch of one walker: the FP64 root vector w^(t0+1) of its walk
-// (the canonical start of the exact fallback) and the centre cache sigma.
+// (the canonical start of the exact fallback) and the centre cache sigma:
+// sigma[t][i] holds the fold of the centre of level t down to index i.
 struct WalkerLayout {
     int Kmax, dimPad;
     __host__ __device__ int64_t bytes() const {
@@ -253,31 +257,29 @@ struct WalkerLayout {
 };
 
 // Level state of one walker in shared memory: for each level t on the
-// current path, the value u being explored there, the zig-zag state, the
-// quantised x, the centre y_t and the parent's norm rho_{t+1}.
+// current path, the value u being explored there (also as a double), the
+// zig-zag state, the quantised x, the centre y_t and the parent's norm
+// rho_{t+1}.  One base pointer; the arrays follow each other.
 struct Levels {
-    double* y;
-    double* rho;
-    int* xq;
-    short* u;
-    short* u1;
-    short* zi;
-    unsigned char* meta;
-    unsigned char* J;
+    unsigned char* base;
+    int K;
+    __device__ __forceinline__ double& y(int t) const { return reinterpret_cast<double*>(base)[t]; }
+    __device__ __forceinline__ double& rho(int t) const { return reinterpret_cast<double*>(base)[K + t]; }
+    __device__ __forceinline__ double& ud(int t) const { return reinterpret_cast<double*>(base)[2 * K + t]; }
+    __device__ __forceinline__ int& xq(int t) const { return reinterpret_cast<int*>(base + 24 * K)[t]; }
+    __device__ __forceinline__ short& u(int t) const { return reinterpret_cast<short*>(base + 28 * K)[t]; }
+    __device__ __forceinline__ short& u1(int t) const { return reinterpret_cast<short*>(base + 30 * K)[t]; }
+    __device__ __forceinline__ short& zi(int t) const { return reinterpret_cast<short*>(base + 32 * K)[t]; }
+    __device__ __forceinline__ unsigned char& meta(int t) const { return base[34 * K + t]; }
+    __device__ __forceinline__ unsigned char& J(int t) const { return base[35 * K + t]; }
 };
 
-__host__ __device__ inline int level_bytes(int Kmax) { return (Kmax * 28 + 15) / 16 * 16; }
+__host__ __device__ inline int level_bytes(int Kmax) { return (Kmax * 36 + 15) / 16 * 16; }
 
 __device__ __forceinline__ Levels levels_at(unsigned char* base, int Kmax) {
     Levels L;
-    L.y = reinterpret_cast<double*>(base);
-    L.rho = L.y + Kmax;
-    L.xq = reinterpret_cast<int*>(L.rho + Kmax);
-    L.u = reinterpret_cast<short*>(L.xq + Kmax);
-    L.u1 = L.u + Kmax;
-    L.zi = L.u1 + Kmax;
-    L.meta = reinterpret_cast<unsigned char*>(L.zi + Kmax);
-    L.J = L.meta + Kmax;
+    L.base = base;
+    L.K = Kmax;
     return L;
 }
 
@@ -347,7 +349,7 @@ __device__ __noinline__ int leaf_check(const Pools& P, const EnumCfg& cfg, int i
         long long a = 0;
         if (c < dim) {
             a = (long long)u * kb[c];
-            for (int j = 1; j < dd; ++j) a += (long long)L.u[j] * kb[(int64_t)j * dim + c];
+            for (int j = 1; j < dd; ++j) a += (long long)L.u(j) * kb[(int64_t)j * dim + c];
         }
         v[q] = a;
     }
@@ -420,7 +422,7 @@ __device__ __noinline__ double canonical_l1(const double* __restrict__ bhat, con
         if (c < dim) {
             double w = root_w[c];
             for (int j = t0; j > t; --j)
-                w = __fma_rn(__dadd_rn(i2d_exact(L.u[j]), L.y[j]), bhat[(int64_t)j * dim + c], w);
+                w = __fma_rn(__dadd_rn(L.ud(j), L.y(j)), bhat[(int64_t)j * dim + c], w);
             w = __fma_rn(x, bhat[(int64_t)t * dim + c], w);
             sl = __dadd_rn(sl, fabs(w));
         }
@@ -437,254 +439,314 @@ __device__ __noinline__ int donate(const Pools& P, int inst, int64_t gid, const 
                                    const double* __restrict__ bhat, int t0, int t, int dd, int dim, int Kmax,
                                    unsigned gmask) {
     const int lg = threadIdx.x & (G - 1);
+    if (P.don_cap <= 0) return 0;
     int h = -1;
     for (int l = t0; l > t; --l)
-        if (!(L.meta[l] & kDonated)) { h = l; break; }
+        if (!(L.meta(l) & kDonated)) { h = l; break; }
     if (h < 0) return 0;
+    // reserve ring index k (slot k mod cap); the slot is free once its
+    // sequence number equals k (set by the consumer of index k - cap)
     long long slot = -1;
     if (lg == 0) {
         for (int tries = 0; tries < 64; ++tries) {
             const unsigned long long old = *(volatile unsigned long long*)&P.ctrl->dtail;
-            if ((int64_t)old >= P.don_cap) break;
+            const unsigned long long head = *(volatile unsigned long long*)&P.ctrl->dhead;
+            if (old - head >= (unsigned long long)P.don_cap) break;   // ring full
+            if (*(volatile unsigned long long*)&P.don_seq[old % P.don_cap] != old) break;   // slot still being read
             if (atomicCAS(&P.ctrl->dtail, old, old + 1) == old) { slot = (long long)old; break; }
         }
     }
     slot = __shfl_sync(gmask, slot, 0, G);
     if (slot < 0) return 0;
+    const long long k = slot;
+    slot = k % P.don_cap;
     char* sp = P.don + slot * P.don_stride;
     int32_t* su = reinterpret_cast<int32_t*>(sp + sizeof(DonHdr));
     double* sw = reinterpret_cast<double*>(sp + ((int64_t)sizeof(DonHdr) + (int64_t)Kmax * 4 + 15) / 16 * 16);
     if (lg == 0) {
         DonHdr hd;
-        hd.inst = inst; hd.t = h; hd.u = L.u[h]; hd.u1 = L.u1[h];
-        hd.zi = L.zi[h]; hd.meta = L.meta[h] & ~kDonated; hd.gid = gid;
-        hd.y = L.y[h]; hd.rhoP = L.rho[h];
+        hd.inst = inst; hd.t = h; hd.u = L.u(h); hd.u1 = L.u1(h);
+        hd.zi = L.zi(h); hd.meta = L.meta(h) & ~kDonated; hd.gid = gid;
+        hd.y = L.y(h); hd.rhoP = L.rho(h);
         *reinterpret_cast<DonHdr*>(sp) = hd;
     }
-    for (int i = h + 1 + lg; i < dd; i += G) su[i] = L.u[i];
+    for (int i = h + 1 + lg; i < dd; i += G) su[i] = L.u(i);
     // canonical FP64 w^(h+1): the chain from the root down to level h+1
     for (int c = lg; c < dim; c += G) {
         double w = root_w[c];
         for (int j = t0; j > h; --j)
-            w = __fma_rn(__dadd_rn(i2d_exact(L.u[j]), L.y[j]), bhat[(int64_t)j * dim + c], w);
+            w = __fma_rn(__dadd_rn(L.ud(j), L.y(j)), bhat[(int64_t)j * dim + c], w);
         sw[c] = w;
     }
     __threadfence();
     __syncwarp(gmask);
     if (lg == 0) {
-        atomicExch(&P.don_ready[slot], 1u);
-        L.meta[h] |= kDonated;
+        atomicExch(&P.don_seq[slot], (unsigned long long)k + 1);   // full for index k
+        L.meta(h) |= kDonated;
+        atomicAdd(&P.ctrl->donations, 1ULL);
     }
     __syncwarp(gmask);
     return 1;
 }
 // walk actions
-constexpr int kNext = 0, kDescend = 1, kUp = 2, kEval = 3;
+constexpr int kNext = 0, kDescend = 1, kUp = 2, kEval = 3, kEnter = 4;
 
-// The walk state machine of one group of G lanes.  Lane l owns the
-// coordinates c = l + G q (q < CPL) of the integer vector
+// Walk state of one group of G lanes.  Lane l owns the coordinates
+// c = l + G q (q < CPL) of the integer vector
 //   W = sum_j Xq_j Bq_j  ~  w^(t+1) 2^(sx+sb),
-// exact and therefore reversible: stepping back to level t subtracts that
-// level's term instead of reloading a stored vector.  E bounds (in units of
-// 2^-(sx+sb)) the distance of ||W||_1 from the exact ||w||_1:
-//   per level: (n+1)(|Xq| + 1)/2 + sum_c |Bq_c| + 1, plus (n+1) for rounding the root.
+// which is exact and therefore reversible: stepping back to level t
+// subtracts that level's term instead of reloading a stored vector.  E bounds
+// (in units of 2^-(sx+sb)) the distance of the filter's ||w||_1 from the
+// exact one: per level (n+1)(|Xq| + 1)/2 + sum_c |Bq_c| + 1, (n+1) for
+// rounding the root, and (n+1) 2^kHiShift for summing T >> kHiShift.
 // The Hoelder decision of the FP64 method, rho > ||w||_1 + eps, is taken from
-// W whenever the margin exceeds the bound; otherwise the canonical FP64 w is
-// rebuilt from the walk's root and the decision is taken exactly as the
-// FP64 arithmetic takes it.
+// the filter whenever the margin exceeds the bound; otherwise the canonical
+// FP64 w is rebuilt from the walk's root and the decision is the FP64 one.
+//
+// All groups of a warp run one flat loop in lockstep: every iteration each
+// group performs one step of its own state machine (fetch work, or evaluate
+// one node and move), so the groups re-converge at the top of every step
+// and the three FP64 operations of a node (x, x^2, rho) are issued once per
+// warp for all 32/G walkers -- the FP64 pipe charges per warp instruction.
+constexpr int kHiShift = 27;   // sum |T| >> 27 in int32: ||w||_1 2^23 < 2^31
+
+enum : int { kFetch = 0, kWalk = 1, kDone = 2 };
+
+// Minimum resident blocks per SM requested from the register allocator:
+// two blocks for groups of 8 or more lanes (measured best on GB300); the
+// 4-lane groups carry 16+ coordinates per lane and keep one block.
+#ifndef MSP_ENUM_MIN_BLOCKS
+#define MSP_ENUM_MIN_BLOCKS(g) ((g) >= 8 ? 2 : 1)
+#endif
+
 template <int G, int CPL>
-__global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* scratch, WalkerLayout WL) {
+__global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
+    enum_kernel(Pools P, EnumCfg cfg, char* scratch, WalkerLayout WL) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lg = threadIdx.x & (G - 1);
     const unsigned gmask = group_mask<G>();
     const int wib = threadIdx.x / G;
     const int64_t walker = (int64_t)blockIdx.x * (blockDim.x / G) + wib;
-    const int Kmax = WL.Kmax, dimPad = WL.dimPad, S = Kmax + 1;
+    const int Kmax = WL.Kmax, dimPad = WL.dimPad;
     const Levels L = levels_at(smem + (int64_t)wib * level_bytes(Kmax), Kmax);
     char* ws = scratch + walker * WL.bytes();
     double* root_w = reinterpret_cast<double*>(ws);
     double* sigma = root_w + dimPad;
     Ctrl* ctrl = P.ctrl;
-
     const int64_t total = P.qbase[P.count];
-    bool static_done = false;   // meaningful in lane 0 only
+
+    // ---- per-walk state (uniform over the group's lanes) ----
+    int state = kFetch;
+    bool static_done = false;          // lane 0: the split queue is exhausted
+    int idle_reg = 0;                  // counted in ctrl->idle (uniform over the group)
+    int inst = 0, dd = 0, dim = 0, sx = 0, Sf = 0, t0 = 0, t = 0;
+    int64_t gid = 0;
+    long long Rbits = 0, eps_fix = 0, ehalf = 0;
+    double eps = 0.0;
+    const double* muT = nullptr;
+    const double* Btab = nullptr;
+    const double* bhat = nullptr;
+    const int32_t* bqtab = nullptr;
+    const int64_t* nbqtab = nullptr;
+    double y = 0.0, rhoP = 0.0, Bt = 0.0;
+    int u = 0, u1 = 0, s = 1, zi = 1, dir = 0, act = kEval;
+    bool onedir = false, zp = true;
+    long long Epar = 0, nbq_t = 0;
+    long long W[CPL], T[CPL];
+    int bq[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) { W[q] = 0; T[q] = 0; bq[q] = 0; }
+    unsigned long long nodes = 0, passed = 0, cfma = 0;
+    unsigned leaves = 0, fallbacks = 0;
+    int item_sols = 0;
+    unsigned spins = 0;
+    const long long life0 = clock64();
+    long long walk0 = 0;
+
     for (;;) {
-        // ---- obtain work: a split prefix, else a donated sibling range ----
-        int src = 0;
-        long long id = 0;
-        if (lg == 0) {
-            if (!static_done) {
-                const unsigned long long it = atomicAdd(&ctrl->qhead, 1ULL);
-                if ((int64_t)it < total) {
-                    src = 1;
-                    id = (long long)it;
-                    atomicAdd(&ctrl->busy, 1);
-                } else {
-                    static_done = true;
+        // ================= fetch: one non-blocking attempt per step =========
+        // (a walker already waiting for donated work polls every 32nd step)
+        if (state == kFetch && (!idle_reg || ((++spins & 31) == 0))) {
+            int src = 0, quit = 0;
+            long long id = 0;
+            if (lg == 0) {
+                if (!static_done) {
+                    const unsigned long long it = atomicAdd(&ctrl->qhead, 1ULL);
+                    if ((int64_t)it < total) {
+                        src = 1;
+                        id = (long long)it;
+                    } else {
+                        static_done = true;
+                    }
                 }
-            }
-            if (src == 0) {
-                atomicAdd(&ctrl->idle, 1);
-                for (;;) {
-                    if (*(volatile unsigned*)&ctrl->stop) break;
+                if (src == 0 && static_done) {
+                    if (!idle_reg) { atomicAdd(&ctrl->idle, 1); idle_reg = 1; }
                     const unsigned long long h = *(volatile unsigned long long*)&ctrl->dhead;
                     const unsigned long long tl = *(volatile unsigned long long*)&ctrl->dtail;
-                    if (h < tl) {
-                        if (atomicCAS(&ctrl->dhead, h, h + 1) == h) {
-                            atomicAdd(&ctrl->busy, 1);
-                            src = 2;
-                            id = (long long)h;
+                    if (h < tl && atomicCAS(&ctrl->dhead, h, h + 1) == h) {
+                        src = 2;
+                        id = (long long)h;
+                    } else if (*(volatile unsigned*)&ctrl->stop) {
+                        quit = 1;
+                    } else if (h >= tl && *(volatile int*)&ctrl->busy == 0 &&
+                               *(volatile unsigned long long*)&ctrl->dhead ==
+                                   *(volatile unsigned long long*)&ctrl->dtail) {
+                        quit = 1;   // nothing left anywhere
+                    } else if ((spins & 255) == 0 && global_time_ns() > ctrl->deadline_ns) {
+                        atomicExch(&ctrl->stop, 2u);
+                        quit = 1;
+                    }
+                }
+                if (src == 2) {   // the donor finishes writing the slot right after reserving it
+                    const unsigned long long k = (unsigned long long)id;
+                    id = (long long)(k % P.don_cap);
+                    unsigned waited = 0;
+                    while (*(volatile unsigned long long*)&P.don_seq[id] != k + 1) {
+                        if ((++waited & 1023) == 0 && global_time_ns() > ctrl->deadline_ns) {
+                            atomicExch(&ctrl->stop, 2u);
+                            src = 0;
+                            quit = 1;
                             break;
                         }
-                        continue;
                     }
-                    if (*(volatile int*)&ctrl->busy == 0 &&
-                        *(volatile unsigned long long*)&ctrl->dhead == *(volatile unsigned long long*)&ctrl->dtail)
-                        break;   // nothing left anywhere
-                    if (global_time_ns() > ctrl->deadline_ns) {
-                        atomicExch(&ctrl->stop, 2u);
-                        break;
-                    }
-                    __nanosleep(1000);
+                    __threadfence();
                 }
-                atomicSub(&ctrl->idle, 1);
-            }
-            if (src == 2) {   // wait until the donor has written the slot
-                while (!*(volatile unsigned*)&P.don_ready[id]) {
-                    if (global_time_ns() > ctrl->deadline_ns) {
-                        atomicExch(&ctrl->stop, 2u);
-                        atomicSub(&ctrl->busy, 1);
-                        src = 0;
-                        break;
-                    }
-                    __nanosleep(100);
+                if (src) {
+                    atomicAdd(&ctrl->busy, 1);
+                    if (idle_reg) { atomicSub(&ctrl->idle, 1); idle_reg = 0; }
                 }
-                __threadfence();
+                if (quit && idle_reg) { atomicSub(&ctrl->idle, 1); idle_reg = 0; }
             }
-        }
-        src = __shfl_sync(gmask, src, 0, G);
-        id = __shfl_sync(gmask, id, 0, G);
-        if (src == 0) break;
-
-        // ---- set up the walk ----
-        int inst;
-        int64_t gid;
-        if (src == 1) {
-            gid = P.qperm ? P.qperm[id] : (int64_t)id;
-            int lo = 0, hi = P.count;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (P.qbase[mid] <= gid) lo = mid; else hi = mid;
-            }
-            inst = lo;
-        } else {
-            const DonHdr* hd = reinterpret_cast<const DonHdr*>(P.don + id * P.don_stride);
-            inst = hd->inst;
-            gid = hd->gid;
-        }
-        const InstDesc& I = P.inst[inst];
-        const int dd = I.dd, dim = I.dim;
-        const int sx = I.sx, Sf = I.sx + I.sb;
-        const double* __restrict__ muT = P.muT + I.offMuT;
-        const double* __restrict__ Btab = P.B + I.offB;
-        const double* __restrict__ bhat = P.bhat + I.offBhat;
-        const int32_t* __restrict__ bqtab = P.bq + I.offBq;
-        const int64_t* __restrict__ nbqtab = P.nbq + I.offNbq;
-        const double eps = slack_of(dim, cfg.use_eps);
-        const long long Rbits = __double_as_longlong((double)dim + eps);
-        const long long eps_fix = (long long)dim << (Sf - 20);   // eps 2^(sx+sb), exact
-        const long long ehalf = dim;                              // (n+1)
-
-        int t0;
-        double y = 0.0, rhoP;
-        int u = 0, u1 = 0, s = 1, zi = 1, dir = 0;
-        bool onedir = false, zp = true;
-        int act;
-        if (src == 1) {
-            const int split_level = I.split_level;
-            t0 = split_level - 1;
-            const int64_t fo = frontier_index(P, inst, I.front_sel, gid - P.qbase[inst]);
-            const int32_t* pu = P.fu + fo * P.Kmax;
-            for (int i = split_level; i < dd; ++i) {
-                const int32_t v = pu[i];
-                if (lg == 0) L.u[i] = (short)v;
-                zp = zp && (v == 0);
-            }
-            for (int c = lg; c < dim; c += G) root_w[c] = P.fw[fo * P.dimPad + c];
-            rhoP = P.frho[fo];
-            act = kEval;   // fresh level: entered below
-        } else {
-            const char* slot = P.don + id * P.don_stride;
-            const DonHdr hd = *reinterpret_cast<const DonHdr*>(slot);
-            const int32_t* su = reinterpret_cast<const int32_t*>(slot + sizeof(DonHdr));
-            const double* sw = reinterpret_cast<const double*>(
-                slot + ((int64_t)sizeof(DonHdr) + (int64_t)Kmax * 4 + 15) / 16 * 16);
-            t0 = hd.t;
-            for (int i = t0 + 1 + lg; i < dd; i += G) L.u[i] = (short)su[i];
-            for (int c = lg; c < dim; c += G) root_w[c] = sw[c];
-            rhoP = hd.rhoP;
-            y = hd.y;
-            u = hd.u;
-            u1 = hd.u1;
-            onedir = hd.meta & kOneDir;
-            s = (hd.meta & kNegS) ? -1 : 1;
-            zp = (hd.meta & kZeroPrefix) != 0;
-            if (onedir) dir = hd.zi; else zi = hd.zi;
-            act = kNext;   // the donor evaluated u already
-        }
-        for (int i = lg; i <= t0; i += G) L.J[i] = (unsigned char)(dd - 1);
-        for (int i = lg; i < dd; i += G) sigma[(int64_t)i * S + dd] = 0.0;
-        if (lg == 0) L.meta[t0] = 0;
-        __syncwarp(gmask);
-        // integer root vector, error bound, and the table row of level t0
-        long long W[CPL];
-        int bq[CPL];
+            src = __shfl_sync(gmask, src, 0, G);
+            id = __shfl_sync(gmask, id, 0, G);
+            quit = __shfl_sync(gmask, quit, 0, G);
+            idle_reg = __shfl_sync(gmask, idle_reg, 0, G);   // uniform over the group
+            if (quit) state = kDone;
+            if (src) {
+                // ---- set up a walk ----
+                if (src == 1) {
+                    gid = P.qperm ? P.qperm[id] : (int64_t)id;
+                    int lo = 0, hi = P.count;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (P.qbase[mid] <= gid) lo = mid; else hi = mid;
+                    }
+                    inst = lo;
+                } else {
+                    const DonHdr* hd = reinterpret_cast<const DonHdr*>(P.don + id * P.don_stride);
+                    inst = hd->inst;
+                    gid = hd->gid;
+                }
+                const InstDesc& I = P.inst[inst];
+                dd = I.dd;
+                dim = I.dim;
+                sx = I.sx;
+                Sf = I.sx + I.sb;
+                muT = P.muT + I.offMuT;
+                Btab = P.B + I.offB;
+                bhat = P.bhat + I.offBhat;
+                bqtab = P.bq + I.offBq;
+                nbqtab = P.nbq + I.offNbq;
+                eps = slack_of(dim, cfg.use_eps);
+                Rbits = __double_as_longlong((double)dim + eps);
+                eps_fix = (long long)dim << (Sf - 20);   // eps 2^(sx+sb), exact
+                ehalf = dim;
+                zp = true;
+                if (src == 1) {
+                    const int split_level = I.split_level;
+                    t0 = split_level - 1;
+                    const int64_t fo = frontier_index(P, inst, I.front_sel, gid - P.qbase[inst]);
+                    const int32_t* pu = P.fu + fo * P.Kmax;
+                    for (int i = split_level; i < dd; ++i) {
+                        const int32_t v = pu[i];
+                        if (lg == 0) { L.u(i) = (short)v; L.ud(i) = (double)v; }
+                        zp = zp && (v == 0);
+                    }
+                    for (int c = lg; c < dim; c += G) root_w[c] = P.fw[fo * P.dimPad + c];
+                    rhoP = P.frho[fo];
+                } else {
+                    const char* slot = P.don + id * P.don_stride;
+                    const DonHdr hd = *reinterpret_cast<const DonHdr*>(slot);
+                    const int32_t* su = reinterpret_cast<const int32_t*>(slot + sizeof(DonHdr));
+                    const double* sw = reinterpret_cast<const double*>(
+                        slot + ((int64_t)sizeof(DonHdr) + (int64_t)Kmax * 4 + 15) / 16 * 16);
+                    t0 = hd.t;
+                    for (int i = t0 + 1 + lg; i < dd; i += G) { L.u(i) = (short)su[i]; L.ud(i) = (double)su[i]; }
+                    for (int c = lg; c < dim; c += G) root_w[c] = sw[c];
+                    __syncwarp(gmask);
+                    if (lg == 0) {   // slot read: free it for ring index (k + cap)
+                        __threadfence();
+                        const unsigned long long k = *(volatile unsigned long long*)&P.don_seq[id] - 1;
+                        atomicExch(&P.don_seq[id], k + (unsigned long long)P.don_cap);
+                    }
+                    rhoP = hd.rhoP;
+                    y = hd.y;
+                    u = hd.u;
+                    u1 = hd.u1;
+                    onedir = hd.meta & kOneDir;
+                    s = (hd.meta & kNegS) ? -1 : 1;
+                    zp = (hd.meta & kZeroPrefix) != 0;
+                    if (onedir) dir = hd.zi; else zi = hd.zi;
+                }
+                for (int i = lg; i <= t0; i += G) L.J(i) = (unsigned char)(dd - 1);
+                if (lg == 0) L.meta(t0) = 0;
+                __syncwarp(gmask);
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) {
-            const int c = lg + G * q;
-            W[q] = (c < dim) ? llrint(ldexp(root_w[c], Sf)) : 0LL;
-        }
-        long long Epar = ehalf;
-        int t = t0;
-        double Bt = Btab[t];
-        long long nbq_t = nbqtab[t];
+                for (int q = 0; q < CPL; ++q) {
+                    const int c = lg + G * q;
+                    W[q] = (c < dim) ? llrint(ldexp(root_w[c], Sf)) : 0LL;
+                }
+                Epar = ehalf;
+                t = t0;
+                Bt = Btab[t];
+                nbq_t = nbqtab[t];
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) bq[q] = bqtab[(int64_t)t * dimPad + lg + G * q];
-
-        unsigned long long nodes = 0, passed = 0, leaves = 0, cfma = 0, fallbacks = 0;
-        int item_sols = 0;
-        bool abort = false;
-
-        // entering level t: centre by the cached fold, start of the zig-zag
-        auto enter_level = [&]() {
-            const int Jt = L.J[t];
-            double acc = sigma[(int64_t)t * S + Jt + 1];
-            for (int i = Jt; i > t; --i) {
-                acc = __fma_rn(i2d_exact(L.u[i]), muT[(int64_t)t * dd + i], acc);
-                sigma[(int64_t)t * S + i] = acc;
+                for (int q = 0; q < CPL; ++q) bq[q] = (lg + G * q < dim) ? bqtab[(int64_t)t * dimPad + lg + G * q] : 0;
+                nodes = passed = leaves = cfma = fallbacks = 0;
+                item_sols = 0;
+                state = kWalk;
+                walk0 = clock64();
+                if (src == 1) {
+                    act = kEnter;
+                } else {
+                    act = kNext;   // the donor evaluated u already
+                }
             }
-            y = acc;
-            cfma += (unsigned long long)(Jt - t);
-            if (t > 0 && L.J[t - 1] < Jt) L.J[t - 1] = (unsigned char)Jt;
-            L.J[t] = (unsigned char)t;
-            const double cstar = -y;
-            const double r1 = rint(cstar);
-            if (fabs(r1) >= (double)kUMax) abort = true;
-            u1 = abort ? 0 : (int)r1;
-            s = (cstar >= r1) ? 1 : -1;
-            onedir = false; dir = 0; zi = 1;
-            if (zp && cfg.sym) { u1 = 0; onedir = true; dir = 1; }
-            u = u1;
-            if (t > 0 && L.J[t - 1] < t) L.J[t - 1] = (unsigned char)t;
-        };
-        if (src == 1) { __syncwarp(gmask); enter_level(); }
+        }
 
-        while (!abort) {
-            if (act == kNext) {
+        // ================= walk: one node per step ==========================
+        if (state == kWalk) {
+            bool abort = false;
+            __syncwarp(gmask);   // level state written by lane 0 in the previous step
+            if (act == kEnter) {
+                // entering level t: centre by the cached fold, start of the zig-zag
+                const int Jt = L.J(t);
+                double* srow = sigma + (int64_t)t * (Kmax + 1);
+                double acc = (Jt + 1 < dd) ? srow[Jt + 1] : 0.0;
+                for (int i = Jt; i > t; --i) {
+                    acc = __fma_rn(L.ud(i), muT[(int64_t)t * dd + i], acc);
+                    srow[i] = acc;
+                }
+                y = acc;
+                cfma += (unsigned long long)(Jt - t);
+                if (lg == 0) {
+                    if (t > 0 && L.J(t - 1) < max(Jt, t)) L.J(t - 1) = (unsigned char)max(Jt, t);
+                    L.J(t) = (unsigned char)t;
+                }
+                const double cstar = -y;
+                const double r1 = rint(cstar);
+                if (fabs(r1) >= (double)kUMax) abort = true;
+                u1 = abort ? 0 : (int)r1;
+                s = (cstar >= r1) ? 1 : -1;
+                onedir = false; dir = 0; zi = 1;
+                if (zp && cfg.sym) { u1 = 0; onedir = true; dir = 1; }
+                u = u1;
+            } else if (act == kNext) {
                 if (onedir) u += dir;
                 else { ++zi; u = zigzag(u1, s, zi); }
-                if (t > 0 && L.J[t - 1] < t) L.J[t - 1] = (unsigned char)t;
+                if (lg == 0 && t > 0 && L.J(t - 1) < t) L.J(t - 1) = (unsigned char)t;
             }
+            __syncwarp(gmask);
             if ((nodes & 1023) == 1023) {
                 // stop flag, time cap, and donation to idle walkers
                 int st = 0, want = 0;
@@ -701,142 +763,148 @@ __global__ void __launch_bounds__(256) enum_kernel(Pools P, EnumCfg cfg, char* s
                         want = qd < (unsigned long long)idle;
                     }
                 }
-                if (__shfl_sync(gmask, st, 0, G)) { abort = true; break; }
-                if (__shfl_sync(gmask, want, 0, G))
+                if (__shfl_sync(gmask, st, 0, G)) abort = true;
+                else if (__shfl_sync(gmask, want, 0, G))
                     donate<G>(P, inst, gid, L, root_w, bhat, t0, t, dd, dim, Kmax, gmask);
             }
-            if (u >= kUMax || u <= -kUMax) { abort = true; set_status(const_cast<InstDesc&>(I), ST_EOVERFLOW); break; }
-            // ---- node (t, u): centre, norm (FP64, the canonical operations) ----
-            const double x = __dadd_rn(i2d_exact(u), y);
-            const double rho = __fma_rn(__dmul_rn(x, x), Bt, rhoP);
-            ++nodes;
-            long long T[CPL];
-            long long Ech = 0;
-            int xq = 0;
-            if (__double_as_longlong(rho) > Rbits) {   // norm test on the bit patterns (rho >= 0)
-                act = kUp;
-            } else {
-                ++passed;
-                if (t == 0) {
-                    ++leaves;
-                    item_sols += leaf_check<G, CPL>(P, cfg, inst, L, u, gmask);
-                    act = kNext;
+            if (u >= kUMax || u <= -kUMax) {
+                if (!abort && lg == 0) set_status(P.inst[inst], ST_EOVERFLOW);
+                abort = true;
+            }
+            bool finished = abort;
+            if (!abort) {
+                // ---- node (t, u): centre, norm (FP64, the canonical operations) ----
+                const double x = __dadd_rn(i2d_exact(u), y);
+                const double rho = __fma_rn(__dmul_rn(x, x), Bt, rhoP);
+                ++nodes;
+                long long Ech = 0;
+                int xq = 0;
+                if (__double_as_longlong(rho) > Rbits) {   // norm test on the bit patterns (rho >= 0)
+                    act = kUp;
                 } else {
-                    // ---- Hoelder test (Theorem 2) through the exact integer filter ----
-                    xq = (int)fix_trunc(x, sx);
-                    long long lsum = 0;
-#pragma unroll
-                    for (int q = 0; q < CPL; ++q) {
-                        T[q] = W[q] + (long long)xq * (long long)bq[q];
-                        lsum += T[q] < 0 ? -T[q] : T[q];
-                    }
-#pragma unroll
-                    for (int off = G / 2; off >= 1; off >>= 1) lsum += __shfl_xor_sync(gmask, lsum, off, G);
-                    const long long axq = xq < 0 ? -(long long)xq : (long long)xq;
-                    Ech = Epar + ((ehalf * (axq + 1)) >> 1) + nbq_t + 1;
-                    bool fail = false;
-                    if (cfg.hoelder != HOELDER_OFF) {
-                        const long long M = fix_trunc(rho, Sf) - lsum - eps_fix;
-                        const long long Etot = Ech + (Ech >> 10) + (lsum >> 32) + 64;
-                        if (M > Etot) fail = true;
-                        else if (M < -Etot) fail = false;
-                        else {
-                            ++fallbacks;
-                            fail = rho > __dadd_rn(canonical_l1<G, CPL>(bhat, root_w, L, t0, t, x, dim, gmask), eps);
-                        }
-                    }
-                    if (fail && cfg.hoelder == HOELDER_CUT) {
-                        if (onedir) {
-                            act = kUp;
-                        } else {
-                            // first failure: one more regular value, then one direction
-                            ++zi;
-                            u = zigzag(u1, s, zi);
-                            dir = (u > u1) ? 1 : -1;
-                            onedir = true;
-                            if (L.J[t - 1] < t) L.J[t - 1] = (unsigned char)t;
-                            act = kEval;
-                        }
+                    ++passed;
+                    if (t == 0) {
+                        ++leaves;
+                        item_sols += leaf_check<G, CPL>(P, cfg, inst, L, u, gmask);
+                        act = kNext;
                     } else {
-                        act = fail ? kNext : kDescend;
+                        // ---- Hoelder test (Theorem 2) through the exact integer filter ----
+                        xq = (int)fix_trunc(x, sx);
+                        int lsum = 0;
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) {
+                            T[q] = W[q] + (long long)xq * (long long)bq[q];
+                            lsum += abs((int)(T[q] >> kHiShift));
+                        }
+#pragma unroll
+                        for (int off = G / 2; off >= 1; off >>= 1) lsum += __shfl_xor_sync(gmask, lsum, off, G);
+                        const long long axq = xq < 0 ? -(long long)xq : (long long)xq;
+                        Ech = Epar + ((ehalf * (axq + 1)) >> 1) + nbq_t + 1;
+                        bool fail = false;
+                        if (cfg.hoelder != HOELDER_OFF) {
+                            const long long Lfix = (long long)lsum << kHiShift;
+                            const long long M = fix_trunc(rho, Sf) - Lfix - eps_fix;
+                            const long long Etot = Ech + (Ech >> 10) + (ehalf << kHiShift) + (Lfix >> 32) + 64;
+                            if (M > Etot) fail = true;
+                            else if (M < -Etot) fail = false;
+                            else {
+                                ++fallbacks;
+                                fail = rho > __dadd_rn(canonical_l1<G, CPL>(bhat, root_w, L, t0, t, x, dim, gmask), eps);
+                            }
+                        }
+                        if (fail && cfg.hoelder == HOELDER_CUT) {
+                            if (onedir) {
+                                act = kUp;
+                            } else {
+                                // first failure: one more regular value, then one direction
+                                ++zi;
+                                u = zigzag(u1, s, zi);
+                                dir = (u > u1) ? 1 : -1;
+                                onedir = true;
+                                if (lg == 0 && L.J(t - 1) < t) L.J(t - 1) = (unsigned char)t;
+                                act = kEval;
+                            }
+                        } else {
+                            act = fail ? kNext : kDescend;
+                        }
                     }
                 }
-            }
-            if (act == kDescend) {
-                // save level t; the child becomes the parent of level t-1
-                if (lg == 0) {
-                    L.u[t] = (short)u;
-                    L.u1[t] = (short)u1;
-                    L.zi[t] = (short)(onedir ? dir : zi);
-                    L.meta[t] = (unsigned char)((onedir ? kOneDir : 0) | (s < 0 ? kNegS : 0) | (zp ? kZeroPrefix : 0));
-                    L.xq[t] = xq;
-                    L.y[t] = y;
-                    L.rho[t] = rhoP;
-                }
+                if (act == kDescend) {
+                    // save level t; the child becomes the parent of level t-1
+                    if (lg == 0) {
+                        L.u(t) = (short)u;
+                        L.ud(t) = i2d_exact(u);
+                        L.u1(t) = (short)u1;
+                        L.zi(t) = (short)(onedir ? dir : zi);
+                        L.meta(t) = (unsigned char)((onedir ? kOneDir : 0) | (s < 0 ? kNegS : 0) | (zp ? kZeroPrefix : 0));
+                        L.xq(t) = xq;
+                        L.y(t) = y;
+                        L.rho(t) = rhoP;
+                    }
 #pragma unroll
-                for (int q = 0; q < CPL; ++q) W[q] = T[q];
-                Epar = Ech;
-                rhoP = rho;
-                zp = zp && (u == 0);
-                --t;
-                Bt = Btab[t];
-                nbq_t = nbqtab[t];
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) bq[q] = bqtab[(int64_t)t * dimPad + lg + G * q];
-                __syncwarp(gmask);
-                enter_level();
-                act = kEval;
-                continue;
-            }
-            if (act == kUp) {
-                // step back; subtract each level's term; donated levels are done
-                bool done = false;
-                int meta = 0;
-                do {
-                    if (t == t0) { done = true; break; }
-                    ++t;
-                    meta = L.meta[t];
-                    const int xqt = L.xq[t];
-                    const long long axt = xqt < 0 ? -(long long)xqt : (long long)xqt;
+                    for (int q = 0; q < CPL; ++q) W[q] = T[q];
+                    Epar = Ech;
+                    rhoP = rho;
+                    zp = zp && (u == 0);
+                    --t;
+                    Bt = Btab[t];
                     nbq_t = nbqtab[t];
 #pragma unroll
-                    for (int q = 0; q < CPL; ++q) {
-                        bq[q] = bqtab[(int64_t)t * dimPad + lg + G * q];
-                        W[q] -= (long long)xqt * (long long)bq[q];
+                    for (int q = 0; q < CPL; ++q) bq[q] = (lg + G * q < dim) ? bqtab[(int64_t)t * dimPad + lg + G * q] : 0;
+                    act = kEnter;
+                } else if (act == kUp) {
+                    // step back; subtract each level's term; donated levels are done
+                    int meta = 0;
+                    for (;;) {
+                        if (t == t0) { finished = true; break; }
+                        ++t;
+                        meta = L.meta(t);
+                        const int xqt = L.xq(t);
+                        const long long axt = xqt < 0 ? -(long long)xqt : (long long)xqt;
+                        nbq_t = nbqtab[t];
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) {
+                            bq[q] = (lg + G * q < dim) ? bqtab[(int64_t)t * dimPad + lg + G * q] : 0;
+                            W[q] -= (long long)xqt * (long long)bq[q];
+                        }
+                        Epar -= ((ehalf * (axt + 1)) >> 1) + nbq_t + 1;
+                        if (!(meta & kDonated)) break;
                     }
-                    Epar -= ((ehalf * (axt + 1)) >> 1) + nbq_t + 1;
-                } while (meta & kDonated);
-                if (done) break;
-                u = L.u[t];
-                u1 = L.u1[t];
-                onedir = meta & kOneDir;
-                s = (meta & kNegS) ? -1 : 1;
-                zp = (meta & kZeroPrefix) != 0;
-                if (onedir) dir = L.zi[t]; else zi = L.zi[t];
-                y = L.y[t];
-                rhoP = L.rho[t];
-                Bt = Btab[t];
-                act = kNext;
+                    if (!finished) {
+                        u = L.u(t);
+                        u1 = L.u1(t);
+                        onedir = meta & kOneDir;
+                        s = (meta & kNegS) ? -1 : 1;
+                        zp = (meta & kZeroPrefix) != 0;
+                        if (onedir) dir = L.zi(t); else zi = L.zi(t);
+                        y = L.y(t);
+                        rhoP = L.rho(t);
+                        Bt = Btab[t];
+                        act = kNext;
+                    }
+                }
+            }
+            if (finished) {
+                if (lg == 0) {
+                    if (abort && !(*(volatile unsigned*)&ctrl->stop)) set_status(P.inst[inst], ST_EOVERFLOW);
+                    atomicAdd(&P.cnt[inst].nodes, nodes);
+                    atomicAdd(&P.cnt[inst].passed, passed);
+                    atomicAdd(&P.cnt[inst].leaves, (unsigned long long)leaves);
+                    atomicAdd(&P.cnt[inst].center_fma, cfma);
+                    atomicAdd(&P.cnt[inst].fallbacks, (unsigned long long)fallbacks);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&P.plog_nodes[gid]), nodes);
+                    if (item_sols) atomicAdd(&P.plog_sols[gid], item_sols);
+                    atomicAdd(&ctrl->walk_cycles, (unsigned long long)(clock64() - walk0));
+                    atomicSub(&ctrl->busy, 1);
+                }
+                state = (abort && *(volatile unsigned*)&ctrl->stop) ? kDone : kFetch;
+                state = __shfl_sync(gmask, state, 0, G);
             }
         }
-        if (abort && lg == 0 && !(*(volatile unsigned*)&ctrl->stop)) set_status(const_cast<InstDesc&>(I), ST_EOVERFLOW);
-        if (lg == 0) {
-            atomicAdd(&P.cnt[inst].nodes, nodes);
-            atomicAdd(&P.cnt[inst].passed, passed);
-            atomicAdd(&P.cnt[inst].leaves, leaves);
-            atomicAdd(&P.cnt[inst].center_fma, cfma);
-            atomicAdd(&P.cnt[inst].fallbacks, fallbacks);
-            atomicAdd(reinterpret_cast<unsigned long long*>(&P.plog_nodes[gid]), nodes);
-            if (item_sols) atomicAdd(&P.plog_sols[gid], item_sols);
-            atomicSub(&ctrl->busy, 1);
-        }
-        __syncwarp(gmask);
-        if (abort) {
-            int st = 0;
-            if (lg == 0) st = *(volatile unsigned*)&ctrl->stop != 0;
-            if (__shfl_sync(gmask, st, 0, G)) break;
-        }
+        if (__all_sync(0xffffffffu, state == kDone)) break;
+        if (__all_sync(0xffffffffu, state != kWalk)) __nanosleep(500);   // whole warp waiting for work
     }
+    if (lg == 0) atomicAdd(&ctrl->life_cycles, (unsigned long long)(clock64() - life0));
 }
 
 // ---------------------------------------------------------------------------
@@ -920,6 +988,17 @@ cudaError_t launch_split(const Pools& P, const EnumCfg& cfg, int lanes, int max_
     return cudaGetLastError();
 }
 
+// ring slot k starts free for index k
+__global__ void ring_init_kernel(unsigned long long* seq, int64_t cap) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cap; k += (int64_t)gridDim.x * blockDim.x)
+        seq[k] = (unsigned long long)k;
+}
+
+cudaError_t launch_ring_init(unsigned long long* seq, int64_t cap, cudaStream_t st) {
+    ring_init_kernel<<<64, 256, 0, st>>>(seq, cap);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, cudaStream_t st) {
     start_kernel<<<1, 1, 0, st>>>(ctrl, cap_ns);
     return cudaGetLastError();
@@ -931,8 +1010,13 @@ int enum_blocks_per_sm(int lanes, int threads, int dimMax, int Kmax) {
     const int smem = enum_smem_bytes(lanes, threads, Kmax);
 #define MSP_OCC(g, c)                                                                                 \
     if (lanes == g && cpl == c) {                                                                     \
-        cudaFuncSetAttribute(enum_kernel<g, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);   \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<g, c>, threads, smem);          \
+        if (cudaFuncSetAttribute(enum_kernel<g, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) \
+                != cudaSuccess ||                                                                     \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<g, c>, threads, smem) !=     \
+                cudaSuccess) {                                                                        \
+            cudaGetLastError();                                                                       \
+            n = 0;                                                                                    \
+        }                                                                                             \
     }
     MSP_ENUM_SHAPES(MSP_OCC)
 #undef MSP_OCC
@@ -950,7 +1034,8 @@ cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int block
     const int smem = enum_smem_bytes(lanes, threads, Kmax);
 #define MSP_LAUNCH(g, c)                                                                              \
     if (lanes == g && cpl == c) {                                                                     \
-        cudaFuncSetAttribute(enum_kernel<g, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);   \
+        cudaError_t e = cudaFuncSetAttribute(enum_kernel<g, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+        if (e != cudaSuccess) return e;                                                               \
         enum_kernel<g, c><<<blocks, threads, smem, st>>>(P, cfg, scratch, W);                         \
         return cudaGetLastError();                                                                    \
     }

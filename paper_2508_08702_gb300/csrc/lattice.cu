@@ -60,10 +60,12 @@ __device__ __forceinline__ double pick4(const double (&a)[4], int q) {
 // Row k of the Gram-Schmidt data from the exact Gram matrix.  Lane l owns the
 // columns j = l + 32 q (q < 4).  mu_at(j, i) returns mu_ji for j < k.
 // Results: rrow[i] = r_ki, murow[i] = mu_ki (i < k), *Bk = r_kk.
+// With invB (the reduction), mu_ki = r_ki * invB[i] and invB[k] = 1 / r_kk is
+// stored; without it (Eq. (4) for the enumeration tables), mu_ki = r_ki / B[i].
 template <class MuAt>
 __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ Grow, MuAt mu_at,
                                              const double* __restrict__ B, double* rrow, double* murow,
-                                             double* Bk, int lane) {
+                                             double* Bk, int lane, double* invB = nullptr) {
     double acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -72,7 +74,7 @@ __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ 
     }
     for (int i = 0; i < k; ++i) {
         const double rki = __shfl_sync(kFull, pick4(acc, i >> 5), i & 31);
-        const double muki = __ddiv_rn(rki, B[i]);
+        const double muki = invB ? __dmul_rn(rki, invB[i]) : __ddiv_rn(rki, B[i]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int j = lane + 32 * q;
@@ -88,6 +90,7 @@ __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ 
     if (lane == 0) {
         if (rrow) rrow[k] = rkk;
         *Bk = rkk;
+        if (invB) invB[k] = __ddiv_rn(1.0, rkk);
     }
     __syncwarp();
 }
@@ -104,6 +107,7 @@ __global__ void __launch_bounds__(32) lll_kernel(Pools P, double delta, double e
     int64_t* G = P.gram + I.offGram;
     double* mu = P.mu + I.offMu;
     double* r = mu + (int64_t)K * K;
+    double* invB = r + (int64_t)K * K;
     double* B = P.Bl + I.offBl;
     auto mu_at = [&](int j, int i) { return mu[(int64_t)j * K + i]; };
     int32_t st = ST_OK;
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(32) lll_kernel(Pools P, double delta, double e
         if (__any_sync(kFull, ovf)) st = ST_EOVERFLOW;
         __syncwarp();
     }
-    if (st == ST_OK) gso_row_warp(0, G, mu_at, B, r, mu, &B[0], lane);
+    if (st == ST_OK) gso_row_warp(0, G, mu_at, B, r, mu, &B[0], lane, invB);
 
     int k = 1;
     while (st == ST_OK && k < K) {
@@ -135,7 +139,8 @@ __global__ void __launch_bounds__(32) lll_kernel(Pools P, double delta, double e
         // lazy size reduction of b_k
         for (int pass = 0;; ++pass) {
             if (pass > 1000) { st = ST_ECAP; break; }
-            gso_row_warp(k, G + (int64_t)k * K, mu_at, B, r + (int64_t)k * K, mu + (int64_t)k * K, &B[k], lane);
+            gso_row_warp(k, G + (int64_t)k * K, mu_at, B, r + (int64_t)k * K, mu + (int64_t)k * K, &B[k], lane,
+                         invB);
             bool changed = false, ovf = false;
             for (int j = k - 1; j >= 0; --j) {
                 const double mkj = mu[(int64_t)k * K + j];
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(32) lll_kernel(Pools P, double delta, double e
             }
             __syncwarp();
             ++swaps;
-            if (k - 1 == 0) gso_row_warp(0, G, mu_at, B, r, mu, &B[0], lane);
+            if (k - 1 == 0) gso_row_warp(0, G, mu_at, B, r, mu, &B[0], lane, invB);
             k = (k > 1) ? k - 1 : 1;
         } else {
             ++k;

@@ -44,7 +44,8 @@ class msp_stats(C.Structure):
                 ("solutions", C.c_int64), ("prefixes", C.c_int64), ("split_level", C.c_int32),
                 ("kernel_rank", C.c_int32), ("lll_iterations", C.c_int64),
                 ("lll_swaps", C.c_int64), ("split_nodes", C.c_int64), ("split_passed", C.c_int64),
-                ("center_fma", C.c_int64), ("fallbacks", C.c_int64), ("status", C.c_int32),
+                ("center_fma", C.c_int64), ("fallbacks", C.c_int64), ("donations", C.c_int64),
+                ("walker_util", C.c_double), ("status", C.c_int32),
                 ("reserved", C.c_int32),
                 ("ms", C.c_double)]
 

@@ -249,3 +249,20 @@ def test_too_small_scale_is_reported():
     assert res.status == M.MSP_ERANK
     assert all(s["status"] == M.MSP_ERANK for s in res.stats)
     ctx.close()
+
+
+WIDE = [I.make_instance(6000 + m + n, m, n, D, tag=f"wide_m{m}n{n}")
+        for (m, n, D) in [(20, 70, 100), (16, 70, 100), (24, 90, 100), (28, 100, 50)]]
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+def test_every_lane_count_on_every_width(lanes):
+    """Lattice widths n+1 from 21 to 101 (row padding 32, 64, 96, 128) under
+    every lane count: node counts and solutions equal the oracle's."""
+    insts = WIDE + [x for x in I.batch_m4_7(8) if x.m <= 5] + SMALL[:3]
+    res, sols, ctx = run_gpu(insts, lanes=lanes)
+    for i, inst in enumerate(insts):
+        ref = O.solve(inst.A, inst.d, lanes=lanes).result
+        assert np.array_equal(sols[i], ref.solutions), (i, inst.tag)
+        assert res.stats[i]["nodes"] == ref.nodes, (i, inst.tag)
+    ctx.close()
