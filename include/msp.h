@@ -208,6 +208,36 @@ MSP_API msp_status msp_phase_ms(msp_ctx *ctx, double *out);
  * second.  Used as the measured peak of the enumeration roofline. */
 MSP_API msp_status msp_fp64_peak(msp_ctx *ctx, double *dfma_per_s);
 
+/* Lattice reduction without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a
+ * library allocate device memory -- a host application whose allocator owns
+ * the whole GPU (a pool that reserved the device up front, or a process under
+ * a hard device-memory cap), or a latency-critical caller that cannot afford
+ * the device-wide synchronisation an allocation may cause.
+ *
+ * It builds the lattice of Eq. (2) for one instance and LLL-reduces it with
+ * the same kernels and the same arithmetic as msp_build_lattice() +
+ * msp_reduce(), so the result equals msp_export_reduced() of that path.
+ *   m, n      1 <= m <= 32, m <= n <= 127; larger sizes return MSP_EINVAL
+ *   A, d      device pointers: A int32 m x n row-major, d int64[m] (inputs)
+ *   N, delta, eta, max_iter   as in msp_opts
+ *   basis     device pointer, int64 (n+1) x (m+n+1) (output, one reduced
+ *             vector per row)
+ *   stream    cudaStream_t (NULL: default stream); the call synchronises it
+ * Returns MSP_OK, MSP_EINVAL, MSP_EOVERFLOW, MSP_ECAP or MSP_ECUDA.
+ *
+ * Scratch: a file-scope device array of 395,520 bytes (Gram matrix,
+ * Gram-Schmidt rows, descriptor for n + 1 <= 128) that every GPU loading this
+ * library holds until the process exits.  No cudaMalloc or cudaFree is
+ * called.  The first call on a device looks up the array's device address
+ * with that device current (one-time set-up); make that first call before
+ * any stream capture.  All calls share the one array: calls that overlap on
+ * the GPU (other streams, other host threads) race and must be serialised
+ * by the caller.  Each call rewrites everything it reads from the array. */
+MSP_API msp_status msp_reduce_lattice_noalloc(int m, int n, const int32_t *A, const int64_t *d, int64_t N,
+                                              double delta, double eta, int64_t max_iter, int64_t *basis,
+                                              void *stream);
+
 /* Human-readable name of a status code, and the context's last error text. */
 MSP_API const char *msp_status_string(int status);
 MSP_API const char *msp_last_error(const msp_ctx *ctx);

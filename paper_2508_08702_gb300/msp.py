@@ -90,6 +90,9 @@ def load():
     L.msp_fp64_peak.restype = C.c_int
     L.msp_phase_ms.argtypes = [P, P]
     L.msp_phase_ms.restype = C.c_int
+    L.msp_reduce_lattice_noalloc.argtypes = [C.c_int, C.c_int, P, P, C.c_int64, C.c_double, C.c_double,
+                                              C.c_int64, P, P]
+    L.msp_reduce_lattice_noalloc.restype = C.c_int
     L.msp_status_string.argtypes = [C.c_int]
     L.msp_status_string.restype = C.c_char_p
     L.msp_last_error.argtypes = [P]
@@ -273,6 +276,20 @@ class Context:
                     "msp_export_prefixes")
         c = cnt.value
         return dict(u=u[:c], rho=rho[:c], nodes=nodes[:c], sols=sols[:c], split_level=int(lvl.value))
+
+
+def msp_reduce_lattice_noalloc(A, d, basis, N: int = 1024, delta: float = 0.99, eta: float = 0.51,
+                               max_iter: int = 2_000_000, stream=None) -> int:
+    """LLL reduction of one instance into the caller's device buffer `basis`
+    ((n+1) x (m+n+1) int64) with no device allocation; A (int32, m x n) and d
+    (int64, m) are CUDA tensors.  Returns the msp_status code."""
+    import torch
+    m, n = A.shape
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(load().msp_reduce_lattice_noalloc(m, n, C.c_void_p(A.data_ptr()), C.c_void_p(d.data_ptr()), N,
+                                                 delta, eta, max_iter, C.c_void_p(basis.data_ptr()),
+                                                 C.c_void_p(stream.cuda_stream)))
 
 
 def solve(instances: Sequence, mode: int = MSP_ALL, time_cap_s: float = 0.0, allow=(MSP_OK,),
