@@ -85,6 +85,8 @@ typedef struct {
                            /*       walkers stop and report MSP_ETIMEOUT when it passes   */
     int64_t donation_capacity; /* [1<<16] slots of the ring through which busy walkers */
                            /*       hand sibling ranges to idle ones (0: no donation)      */
+    int log_features;      /* [0] 1: compute the 32 features of every subtree prefix      */
+                           /*     (msp_export_features), e.g. to train the scorer         */
 } msp_opts;
 
 /* Per-instance results of an enumeration. */
@@ -106,6 +108,8 @@ typedef struct {
                            /* filter, decided by rebuilding the FP64 vector           */
     int64_t donations;     /* batch total only: sibling ranges handed between walkers */
     double walker_util;    /* batch total only: fraction of walker time spent walking */
+    double first_ms;       /* MSP_FIRST: device time from the start of the enumeration */
+                           /* to this instance's first verified solution (-1: none)   */
     int32_t status;        /* msp_status of this instance                              */
     int32_t reserved;
     double ms;             /* wall time of the enumeration call (whole batch)          */
@@ -201,6 +205,47 @@ MSP_API msp_status msp_export_prefixes(msp_ctx *ctx, int inst, int32_t *u, doubl
  * (LLL + Gram-Schmidt, if msp_reduce or msp_run_async queued it), out[1]
  * split, out[2] enumeration kernel, out[3] solution collection. */
 MSP_API msp_status msp_phase_ms(msp_ctx *ctx, double *out);
+
+/* ---- subtree scorer (not in the paper) -----------------------------------
+ * In MSP_FIRST mode the subtrees of a batch are taken in rank order,
+ * interleaving the instances: rank = depth-first position (MSP_PLAIN) or the
+ * position by descending priority of a 3-layer MLP (MSP_LEARNED).  The order
+ * never changes the pruning: MSP_ALL returns the same solutions and node
+ * counts under either order.  Network 32 -> 64 -> 64 -> 8, ReLU, bfloat16
+ * tensor-core products with float32 accumulation; parameters are float32:
+ * W1[32][64] b1[64] W2[64][64] b2[64] W3[64][8] b3[8] (row = input).
+ * Outputs y0 = logit of P(the subtree holds a solution), y1 = predicted
+ * log(1 + nodes of the subtree); priority = log sigmoid(y0) - y1. */
+
+/* Number of float32 parameters of the scorer (6792). */
+MSP_API int msp_mlp_param_count(void);
+
+/* Use the scorer with these parameters (host memory, copied) for
+ * MSP_LEARNED; NULL removes it (MSP_LEARNED then falls back to MSP_PLAIN). */
+MSP_API msp_status msp_set_scorer(msp_ctx *ctx, const float *theta);
+
+/* After an enumeration with opts.log_features (or a learned order): the 32
+ * features of each prefix of instance `inst`, in depth-first order (the
+ * order of msp_export_prefixes), into host memory (cap rows of 32 floats);
+ * *count = number of prefixes. */
+MSP_API msp_status msp_export_features(msp_ctx *ctx, int inst, float *feat, size_t cap, size_t *count);
+
+/* Scorer kernels on device memory (all pointers are device pointers; each
+ * call synchronises the context's stream):
+ *   forward: y[n][8] = mlp(x[n][32])
+ *   grad:    gradient of the mean loss over the n rows (target[n][2] =
+ *            (found 0/1, log(1 + nodes)); loss per row pos_weight*BCE for
+ *            found rows, BCE otherwise, + 0.1 (y1 - target1)^2) into grad,
+ *            mean loss into *loss
+ *   train:   `steps` Adam steps (lr, betas 0.9/0.999, eps 1e-8) on
+ *            mini-batches of 128 rows drawn with replacement by a
+ *            counter-based generator from `seed`; theta is updated in place;
+ *            losses (NULL or steps floats) receives each step's mean loss. */
+MSP_API msp_status msp_mlp_forward(msp_ctx *ctx, const float *theta, const float *x, int64_t n, float *y);
+MSP_API msp_status msp_mlp_grad(msp_ctx *ctx, const float *theta, const float *x, const float *target, int64_t n,
+                                float pos_weight, float *grad, float *loss);
+MSP_API msp_status msp_mlp_train(msp_ctx *ctx, float *theta, const float *x, const float *target, int64_t n,
+                                 int steps, float lr, float pos_weight, uint64_t seed, float *losses);
 
 /* Measure this GPU's FP64 fused multiply-add throughput: a kernel of
  * independent FMA chains on every SM, timed with CUDA events on the

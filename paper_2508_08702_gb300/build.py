@@ -16,7 +16,7 @@ SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmsp_gb300.so")
 ROOT = os.path.dirname(HERE)
-SOURCES = ["api.cu", "lattice.cu", "enum.cu", "peak.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "lattice.cu", "enum.cu", "learn.cu", "mlp.cu", "peak.cu", "noalloc.cu"]
 HEADERS = ["common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",

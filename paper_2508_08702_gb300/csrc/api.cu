@@ -31,6 +31,16 @@ int64_t walker_bytes(int Kmax, int dimPad);
 int64_t donation_slot_bytes(int Kmax, int dimPad);
 int enum_blocks_per_sm(int lanes, int threads, int dimMax, int Kmax);
 int enum_smem_bytes(int lanes, int threads, int Kmax);
+cudaError_t launch_features(const Pools& P, float* prof, float* feat, int sms, cudaStream_t st);
+cudaError_t launch_order(const Pools& P, const float* y, int64_t npad, unsigned long long* keys,
+                         unsigned long long* vals, unsigned long long* keys2, unsigned long long* vals2,
+                         int64_t* perm, int sms, cudaStream_t st, int64_t* launches);
+cudaError_t mlp_forward(const float* theta, const float* X, int64_t n, float* Y, int sms, cudaStream_t st);
+cudaError_t mlp_grad(const float* theta, const float* X, const float* target, int64_t n, float pos_weight,
+                     float* grad, float* loss, cudaStream_t st);
+cudaError_t mlp_train(float* theta, const float* X, const float* target, int64_t n, int steps, float lr,
+                      float pos_weight, uint64_t seed, float* work, float* losses, cudaStream_t st);
+int mlp_param_count();
 cudaError_t fp64_peak(double* dfma_per_s, int sms, cudaStream_t st);
 }  // namespace msp
 
@@ -65,8 +75,11 @@ struct msp_ctx {
     cudaEvent_t evs1 = nullptr, eve1 = nullptr;   // split end, enumerate end
     bool reduce_timed = false;
     // device buffers
-    Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, bq, nbq, fu, frho, fw, fcnt, qbase, sols, ctrl, soff,
-        fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_seq;
+    Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, bq, nbq, fu, fdisc, fxsum, frho, fw, fcnt, qbase, sols, ctrl, soff,
+        fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_seq, feat, prof, yout, skeys, svals, skeys2,
+        svals2, perm, theta, mlpwork;
+    bool scorer_set = false;
+    bool features_valid = false;
     std::vector<int64_t> soff_h;
     std::vector<SolRec> sout_h;
     bool sout_valid = false;
@@ -131,6 +144,8 @@ void refresh_pools(msp_ctx* c) {
     P.fu = ptr<int32_t>(c->fu);
     P.frho = ptr<double>(c->frho);
     P.fw = ptr<double>(c->fw);
+    P.fdisc = ptr<int32_t>(c->fdisc);
+    P.fxsum = ptr<float>(c->fxsum);
     P.F = c->F;
     P.qbase = ptr<int64_t>(c->qbase);
     P.qperm = nullptr;
@@ -188,6 +203,7 @@ void msp_default_opts(msp_opts* o) {
     o->sol_capacity = 1 << 20;
     o->max_seconds = 600.0;
     o->donation_capacity = 1 << 16;
+    o->log_features = 0;
 }
 
 const char* msp_status_string(int s) {
@@ -248,9 +264,10 @@ void msp_destroy(msp_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->st);
     Buf* all[] = {&c->inst, &c->cnt, &c->A, &c->d, &c->basis, &c->gram, &c->mu, &c->Bl, &c->kb, &c->muT, &c->B,
-                  &c->bhat, &c->bq, &c->nbq, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
+                  &c->bhat, &c->bq, &c->nbq, &c->fdisc, &c->fxsum, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
                   &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols, &c->don,
-                  &c->don_seq};
+                  &c->don_seq, &c->feat, &c->prof, &c->yout, &c->skeys, &c->svals, &c->skeys2, &c->svals2,
+                  &c->perm, &c->theta, &c->mlpwork};
     for (Buf* b : all)
         if (b->p) cudaFree(b->p);
     for (cudaEvent_t ev : {c->ev0, c->ev1, c->evr0, c->evr1, c->evs1, c->eve1})
@@ -321,6 +338,8 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     ENSURE(frho, sizeof(double) * (size_t)count * 2 * c->F);
     ENSURE(fw, sizeof(double) * (size_t)count * 2 * c->F * c->dimPad);
     ENSURE(fcnt, sizeof(int64_t) * (size_t)count * c->F);
+    ENSURE(fdisc, sizeof(int32_t) * (size_t)count * 2 * c->F);
+    ENSURE(fxsum, sizeof(float) * (size_t)count * 2 * c->F);
     ENSURE(plog_nodes, sizeof(int64_t) * (size_t)count * c->F);
     ENSURE(plog_sols, sizeof(int32_t) * (size_t)count * c->F);
     ENSURE(don, (size_t)c->o.donation_capacity * donation_slot_bytes(Kmax, c->dimPad));
@@ -333,6 +352,19 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     ENSURE(seg, sizeof(SolRec) * (size_t)c->o.sol_capacity);
     ENSURE(sout, sizeof(SolRec) * (size_t)c->o.sol_capacity);
     ENSURE(scratch, (size_t)walkers * walker_bytes(Kmax, c->dimPad));
+    {
+        const int64_t cap = (int64_t)count * c->F;
+        int64_t npad = 1;
+        while (npad < cap) npad <<= 1;
+        ENSURE(feat, sizeof(float) * 32 * (size_t)cap);
+        ENSURE(prof, sizeof(float) * 17 * (size_t)count);
+        ENSURE(yout, sizeof(float) * 8 * (size_t)cap);
+        ENSURE(skeys, sizeof(unsigned long long) * (size_t)npad);
+        ENSURE(svals, sizeof(unsigned long long) * (size_t)npad);
+        ENSURE(skeys2, sizeof(unsigned long long) * (size_t)npad);
+        ENSURE(svals2, sizeof(unsigned long long) * (size_t)npad);
+        ENSURE(perm, sizeof(int64_t) * (size_t)cap);
+    }
 #undef ENSURE
     refresh_pools(c);
     const cudaMemcpyKind kind = (mem == MSP_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -396,8 +428,38 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
         cudaSuccess)
         return cuda_fail(c, e, "split");
     c->launches += 2;
+    // subtree features and queue order: the first-solution mode interleaves the
+    // instances by rank (depth-first rank, or the scorer's rank when learned)
+    const bool learned = (order == MSP_LEARNED) && c->scorer_set;
+    const bool want_features = c->o.log_features || learned;
+    Pools Pq = c->P;
+    c->features_valid = false;
+    if (want_features) {
+        if ((e = launch_features(c->P, ptr<float>(c->prof), ptr<float>(c->feat), c->sms, c->st)) != cudaSuccess)
+            return cuda_fail(c, e, "features");
+        c->launches += 2;
+        c->features_valid = true;
+    }
+    if (mode == MSP_FIRST || learned) {
+        const int64_t cap = (int64_t)c->count * c->F;
+        int64_t npad = 1;
+        while (npad < cap) npad <<= 1;
+        const float* y = nullptr;
+        if (learned) {
+            if ((e = mlp_forward(ptr<float>(c->theta), ptr<float>(c->feat), cap, ptr<float>(c->yout), c->sms, c->st)) !=
+                cudaSuccess)
+                return cuda_fail(c, e, "scorer");
+            ++c->launches;
+            y = ptr<float>(c->yout);
+        }
+        if ((e = launch_order(c->P, y, npad, ptr<unsigned long long>(c->skeys), ptr<unsigned long long>(c->svals),
+                              ptr<unsigned long long>(c->skeys2), ptr<unsigned long long>(c->svals2),
+                              ptr<int64_t>(c->perm), c->sms, c->st, &c->launches)) != cudaSuccess)
+            return cuda_fail(c, e, "order");
+        Pq.qperm = ptr<int64_t>(c->perm);
+    }
     cudaEventRecord(c->evs1, c->st);
-    if ((e = launch_enum(c->P, cfg, c->o.lanes, blocks, threads, ptr<char>(c->scratch), c->Kmax, c->dimPad, c->st)) !=
+    if ((e = launch_enum(Pq, cfg, c->o.lanes, blocks, threads, ptr<char>(c->scratch), c->Kmax, c->dimPad, c->st)) !=
         cudaSuccess)
         return cuda_fail(c, e, "enumerate");
     ++c->launches;
@@ -460,6 +522,7 @@ msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {
         S.split_passed = (int64_t)cn[i].split_passed;
         S.center_fma = (int64_t)cn[i].center_fma;
         S.fallbacks = (int64_t)cn[i].fallbacks;
+        S.first_ms = (c->last_mode == MSP_FIRST && cn[i].nsol > 0) ? (double)cn[i].first_ns * 1e-6 : -1.0;
         int32_t st = h[i].status;
         if (st == MSP_OK && ctl.stop == 2) st = MSP_ETIMEOUT;
         if (st == MSP_OK && trunc) st = MSP_ETRUNC;
@@ -495,6 +558,68 @@ msp_status msp_enumerate(msp_ctx* c, int mode, int order, double time_cap_s, msp
     msp_status s = queue_enumerate(c, mode, order, time_cap_s);
     if (s != MSP_OK) return s;
     return msp_wait(c, stats, total);
+}
+
+int msp_mlp_param_count(void) { return mlp_param_count(); }
+
+msp_status msp_set_scorer(msp_ctx* c, const float* theta) {
+    if (!c) return MSP_EINVAL;
+    if (!theta) { c->scorer_set = false; return MSP_OK; }
+    msp_status s = ensure(c, c->theta, sizeof(float) * mlp_param_count(), "theta");
+    if (s != MSP_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(c->theta.p, theta, sizeof(float) * mlp_param_count(), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_set_scorer");
+    c->scorer_set = true;
+    return MSP_OK;
+}
+
+msp_status msp_export_features(msp_ctx* c, int inst, float* feat, size_t cap, size_t* count) {
+    if (!c || !count) return MSP_EINVAL;
+    if (c->state < 3 || !c->features_valid) return fail(c, MSP_ESTATE, "msp_export_features: no features logged");
+    if (inst < 0 || inst >= c->count) return fail(c, MSP_EINVAL, "instance index out of range");
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    int64_t q[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(q, ptr<int64_t>(c->qbase) + inst, sizeof q, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_export_features");
+    *count = (size_t)(q[1] - q[0]);
+    const int64_t take = std::min<int64_t>(q[1] - q[0], (int64_t)cap);
+    if (feat && take > 0) {
+        e = cudaMemcpy(feat, ptr<float>(c->feat) + q[0] * 32, sizeof(float) * 32 * take, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "msp_export_features copy");
+    }
+    return MSP_OK;
+}
+
+msp_status msp_mlp_forward(msp_ctx* c, const float* theta, const float* x, int64_t n, float* y) {
+    if (!c || !theta || !x || !y || n < 0) return MSP_EINVAL;
+    cudaError_t e = mlp_forward(theta, x, n, y, c->sms, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_mlp_forward");
+    ++c->launches;
+    return MSP_OK;
+}
+
+msp_status msp_mlp_grad(msp_ctx* c, const float* theta, const float* x, const float* target, int64_t n,
+                        float pos_weight, float* grad, float* loss) {
+    if (!c || !theta || !x || !target || !grad || !loss || n < 1) return MSP_EINVAL;
+    cudaError_t e = mlp_grad(theta, x, target, n, pos_weight, grad, loss, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_mlp_grad");
+    ++c->launches;
+    return MSP_OK;
+}
+
+msp_status msp_mlp_train(msp_ctx* c, float* theta, const float* x, const float* target, int64_t n, int steps,
+                         float lr, float pos_weight, uint64_t seed, float* losses) {
+    if (!c || !theta || !x || !target || n < 1 || steps < 1 || !(lr > 0.f)) return MSP_EINVAL;
+    msp_status s = ensure(c, c->mlpwork, sizeof(float) * 3 * mlp_param_count(), "mlpwork");
+    if (s != MSP_OK) return s;
+    cudaError_t e = mlp_train(theta, x, target, n, steps, lr, pos_weight, seed, ptr<float>(c->mlpwork), losses, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_mlp_train");
+    ++c->launches;
+    return MSP_OK;
 }
 
 msp_status msp_fp64_peak(msp_ctx* c, double* dfma_per_s) {

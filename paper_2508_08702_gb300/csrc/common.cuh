@@ -48,6 +48,7 @@ struct InstCounters {
     unsigned long long split_nodes, split_passed;   // part done by the splitter
     unsigned long long center_fma;                  // centre-fold fmas of the walkers
     unsigned long long fallbacks;                   // Hoelder tests decided by the FP64 rebuild
+    unsigned long long first_ns;                    // first-solution mode: time of the first solution
 };
 
 // A found solution: x_c is bit (127 - c) of the 128-bit key (hi:lo), so that
@@ -79,6 +80,8 @@ struct Pools {
     int32_t* fu;
     double* frho;
     double* fw;
+    int32_t* fdisc;                    // per prefix: levels where u differs from the first zig-zag value
+    float* fxsum;                      // per prefix: sum over its levels of |x|
     int64_t F;
     // work queue
     int64_t* qbase;                    // count + 1 exclusive prefix sums of nprefix
@@ -106,8 +109,11 @@ struct Ctrl {
     unsigned long long life_cycles;    // sum over walkers of clock cycles alive
     unsigned long long nsol_total;     // solutions found (all instances)
     unsigned long long deadline_ns;    // globaltimer deadline, 0 = none
-    unsigned int stop;                 // 1: first solution found, 2: time cap
+    unsigned int stop;                 // 1: every instance solved (first-solution mode), 2: time cap
     int32_t gstatus;                   // batch-wide status
+    unsigned long long start_ns;       // globaltimer at the start of the enumeration
+    int solved;                        // first-solution mode: instances with a solution
+    int active;                        // instances with subtrees to enumerate
 };
 
 // Enumeration options passed to the split and enumeration kernels.

@@ -48,7 +48,7 @@ __device__ __forceinline__ double slack_of(int dim, int use_eps) {
 template <int G, bool WRITE>
 __device__ int64_t expand_parent(const Pools& P, const EnumCfg& cfg, int inst, int dd, int dim, int t,
                                  const int32_t* __restrict__ pu, double prho, const double* __restrict__ pw,
-                                 int out_sel, int64_t base, unsigned long long& nodes,
+                                 int pdisc, float pxsum, int out_sel, int64_t base, unsigned long long& nodes,
                                  unsigned long long& passed, bool& ovf) {
     const InstDesc& I = P.inst[inst];
     const double* muT = P.muT + I.offMuT;
@@ -112,6 +112,8 @@ __device__ int64_t expand_parent(const Pools& P, const EnumCfg& cfg, int inst, i
                 for (int i = 0; i < P.Kmax; ++i) ou[i] = (i > t && i < dd) ? pu[i] : 0;
                 ou[t] = u;
                 P.frho[o] = rho;
+                P.fdisc[o] = pdisc + (u != u1 ? 1 : 0);
+                P.fxsum[o] = pxsum + (float)fabs(x);
                 double* ow = P.fw + o * P.dimPad;
                 for (int c = 0; c < dim; ++c) ow[c] = __fma_rn(x, bhat[(int64_t)t * dim + c], pw[c]);
             }
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int ma
         const int64_t o = frontier_index(P, inst, 0, 0);
         for (int i = threadIdx.x; i < P.Kmax; i += blockDim.x) P.fu[o * P.Kmax + i] = 0;
         for (int c = threadIdx.x; c < P.dimPad; c += blockDim.x) P.fw[o * P.dimPad + c] = 0.0;
-        if (threadIdx.x == 0) P.frho[o] = 0.0;
+        if (threadIdx.x == 0) { P.frho[o] = 0.0; P.fdisc[o] = 0; P.fxsum[o] = 0.f; }
     }
     __syncthreads();
     int sel = 0, t = dd - 1, depth = 0;
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int ma
             const int64_t o = frontier_index(P, inst, sel, p);
             unsigned long long dn = 0, dp = 0;
             cnt[p] = expand_parent<G, false>(P, cfg, inst, dd, dim, t, P.fu + o * P.Kmax, P.frho[o],
-                                             P.fw + o * P.dimPad, sel ^ 1, 0, dn, dp, ovf);
+                                             P.fw + o * P.dimPad, 0, 0.f, sel ^ 1, 0, dn, dp, ovf);
         }
         if (threadIdx.x == 0) s_ovf = 0;
         __syncthreads();
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int ma
         for (int64_t p = threadIdx.x; p < count; p += blockDim.x) {
             const int64_t o = frontier_index(P, inst, sel, p);
             expand_parent<G, true>(P, cfg, inst, dd, dim, t, P.fu + o * P.Kmax, P.frho[o], P.fw + o * P.dimPad,
-                                   sel ^ 1, cnt[p], nodes, passed, ovf);
+                                   P.fdisc[o], P.fxsum[o], sel ^ 1, cnt[p], nodes, passed, ovf);
         }
         __syncthreads();
         sel ^= 1;
@@ -228,16 +230,23 @@ __global__ void start_kernel(Ctrl* c, unsigned long long cap_ns) {
     c->nsol_total = 0;
     c->stop = 0;
     c->gstatus = 0;
-    c->deadline_ns = cap_ns ? global_time_ns() + cap_ns : 0ULL;
+    c->start_ns = global_time_ns();
+    c->deadline_ns = cap_ns ? c->start_ns + cap_ns : 0ULL;
+    c->solved = 0;
+    c->active = 0;
 }
 
 // exclusive prefix sums of the per-instance prefix counts (one thread)
 __global__ void queue_kernel(Pools P) {
     int64_t run = 0;
+    int active = 0;
     for (int i = 0; i < P.count; ++i) {
         P.qbase[i] = run;
-        run += (P.inst[i].status == ST_OK) ? P.inst[i].nprefix : 0;
+        const int64_t k = (P.inst[i].status == ST_OK) ? P.inst[i].nprefix : 0;
+        run += k;
+        active += k > 0;
     }
+    P.ctrl->active = active;
     P.qbase[P.count] = run;
     P.ctrl->qhead = 0;
 }
@@ -402,8 +411,11 @@ __device__ __noinline__ int leaf_check(const Pools& P, const EnumCfg& cfg, int i
             r.inst = inst; r.pad = 0; r.hi = khi; r.lo = klo;
             P.sols[k] = r;
         }
-        atomicAdd(&P.cnt[inst].nsol, 1ULL);
-        if (cfg.first) atomicExch(&P.ctrl->stop, 1u);
+        const unsigned long long prev = atomicAdd(&P.cnt[inst].nsol, 1ULL);
+        if (cfg.first && prev == 0) {   // first solution of this instance
+            P.cnt[inst].first_ns = global_time_ns() - P.ctrl->start_ns;
+            if (atomicAdd(&P.ctrl->solved, 1) + 1 >= P.ctrl->active) atomicExch(&P.ctrl->stop, 1u);
+        }
     }
     return ok ? 1 : 0;
 }
@@ -637,6 +649,22 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     inst = hd->inst;
                     gid = hd->gid;
                 }
+                int skip = 0;
+                if (cfg.first && lg == 0) skip = *(volatile unsigned long long*)&P.cnt[inst].nsol != 0;
+                skip = __shfl_sync(gmask, skip, 0, G);
+                if (skip) {   // instance already solved: drop the subtree
+                    if (lg == 0) {
+                        if (src == 2) {   // release the ring slot
+                            __threadfence();
+                            const unsigned long long k = *(volatile unsigned long long*)&P.don_seq[id] - 1;
+                            atomicExch(&P.don_seq[id], k + (unsigned long long)P.don_cap);
+                        }
+                        atomicSub(&ctrl->busy, 1);
+                    }
+                    src = 0;
+                }
+            }
+            if (src) {
                 const InstDesc& I = P.inst[inst];
                 dd = I.dd;
                 dim = I.dim;
@@ -716,7 +744,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
 
         // ================= walk: one node per step ==========================
         if (state == kWalk) {
-            bool abort = false;
+            bool abort = false, quiet = false;
             __syncwarp(gmask);   // level state written by lane 0 in the previous step
             if (act == kEnter) {
                 // entering level t: centre by the cached fold, start of the zig-zag
@@ -763,7 +791,10 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         want = qd < (unsigned long long)idle;
                     }
                 }
+                int solved = 0;
+                if (cfg.first && lg == 0) solved = *(volatile unsigned long long*)&P.cnt[inst].nsol != 0;
                 if (__shfl_sync(gmask, st, 0, G)) abort = true;
+                else if (__shfl_sync(gmask, solved, 0, G)) { abort = true; quiet = true; }
                 else if (__shfl_sync(gmask, want, 0, G))
                     donate<G>(P, inst, gid, L, root_w, bhat, t0, t, dd, dim, Kmax, gmask);
             }
@@ -886,7 +917,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
             }
             if (finished) {
                 if (lg == 0) {
-                    if (abort && !(*(volatile unsigned*)&ctrl->stop)) set_status(P.inst[inst], ST_EOVERFLOW);
+                    if (abort && !quiet && !(*(volatile unsigned*)&ctrl->stop)) set_status(P.inst[inst], ST_EOVERFLOW);
                     atomicAdd(&P.cnt[inst].nodes, nodes);
                     atomicAdd(&P.cnt[inst].passed, passed);
                     atomicAdd(&P.cnt[inst].leaves, (unsigned long long)leaves);

@@ -36,7 +36,7 @@ class msp_opts(C.Structure):
                 ("split_target", C.c_int), ("split_capacity", C.c_int),
                 ("warps_per_block", C.c_int), ("blocks_per_sm", C.c_int),
                 ("smem_tables", C.c_int), ("sol_capacity", C.c_int64), ("max_seconds", C.c_double),
-                ("donation_capacity", C.c_int64)]
+                ("donation_capacity", C.c_int64), ("log_features", C.c_int)]
 
 
 class msp_stats(C.Structure):
@@ -45,7 +45,7 @@ class msp_stats(C.Structure):
                 ("kernel_rank", C.c_int32), ("lll_iterations", C.c_int64),
                 ("lll_swaps", C.c_int64), ("split_nodes", C.c_int64), ("split_passed", C.c_int64),
                 ("center_fma", C.c_int64), ("fallbacks", C.c_int64), ("donations", C.c_int64),
-                ("walker_util", C.c_double), ("status", C.c_int32),
+                ("walker_util", C.c_double), ("first_ms", C.c_double), ("status", C.c_int32),
                 ("reserved", C.c_int32),
                 ("ms", C.c_double)]
 
@@ -93,6 +93,15 @@ def load():
     L.msp_reduce_lattice_noalloc.argtypes = [C.c_int, C.c_int, P, P, C.c_int64, C.c_double, C.c_double,
                                               C.c_int64, P, P]
     L.msp_reduce_lattice_noalloc.restype = C.c_int
+    L.msp_mlp_param_count.argtypes = []
+    L.msp_mlp_param_count.restype = C.c_int
+    L.msp_set_scorer.argtypes = [P, P]
+    L.msp_export_features.argtypes = [P, C.c_int, P, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.msp_mlp_forward.argtypes = [P, P, P, C.c_int64, P]
+    L.msp_mlp_grad.argtypes = [P, P, P, P, C.c_int64, C.c_float, P, P]
+    L.msp_mlp_train.argtypes = [P, P, P, P, C.c_int64, C.c_int, C.c_float, C.c_float, C.c_uint64, P]
+    for name in ("msp_set_scorer", "msp_export_features", "msp_mlp_forward", "msp_mlp_grad", "msp_mlp_train"):
+        getattr(L, name).restype = C.c_int
     L.msp_status_string.argtypes = [C.c_int]
     L.msp_status_string.restype = C.c_char_p
     L.msp_last_error.argtypes = [P]
@@ -221,6 +230,41 @@ class Context:
         self._check(st, "msp_wait", ok=allow)
         return self._result(st, stats[:self.count], total)
 
+    # -- subtree scorer ---------------------------------------------------------
+    def msp_set_scorer(self, theta):
+        """theta: numpy float32 vector of msp_mlp_param_count() entries, or None."""
+        if theta is None:
+            self._check(self._L.msp_set_scorer(self._h, None), "msp_set_scorer")
+            return
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == self._L.msp_mlp_param_count()
+        self._check(self._L.msp_set_scorer(self._h, _np_ptr(th)), "msp_set_scorer")
+
+    def msp_export_features(self, inst: int) -> np.ndarray:
+        cnt = C.c_size_t()
+        self._check(self._L.msp_export_features(self._h, inst, None, 0, C.byref(cnt)), "msp_export_features")
+        f = np.zeros((max(cnt.value, 1), 32), np.float32)
+        self._check(self._L.msp_export_features(self._h, inst, _np_ptr(f), cnt.value, C.byref(cnt)),
+                    "msp_export_features")
+        return f[:cnt.value]
+
+    def msp_mlp_forward(self, theta, x, y):
+        """Device tensors: theta (P,), x (n, 32), y (n, 8) float32."""
+        self._check(self._L.msp_mlp_forward(self._h, C.c_void_p(theta.data_ptr()), C.c_void_p(x.data_ptr()),
+                                            x.shape[0], C.c_void_p(y.data_ptr())), "msp_mlp_forward")
+
+    def msp_mlp_grad(self, theta, x, target, pos_weight, grad, loss):
+        self._check(self._L.msp_mlp_grad(self._h, C.c_void_p(theta.data_ptr()), C.c_void_p(x.data_ptr()),
+                                         C.c_void_p(target.data_ptr()), x.shape[0], pos_weight,
+                                         C.c_void_p(grad.data_ptr()), C.c_void_p(loss.data_ptr())),
+                    "msp_mlp_grad")
+
+    def msp_mlp_train(self, theta, x, target, steps, lr, pos_weight, seed, losses=None):
+        self._check(self._L.msp_mlp_train(self._h, C.c_void_p(theta.data_ptr()), C.c_void_p(x.data_ptr()),
+                                          C.c_void_p(target.data_ptr()), x.shape[0], steps, lr, pos_weight, seed,
+                                          C.c_void_p(losses.data_ptr()) if losses is not None else None),
+                    "msp_mlp_train")
+
     def msp_fp64_peak(self) -> float:
         out = np.zeros(1, np.float64)
         self._check(self._L.msp_fp64_peak(self._h, _np_ptr(out)), "msp_fp64_peak")
@@ -292,15 +336,21 @@ def msp_reduce_lattice_noalloc(A, d, basis, N: int = 1024, delta: float = 0.99, 
                                                  C.c_void_p(stream.cuda_stream)))
 
 
+def mlp_param_count() -> int:
+    return int(load().msp_mlp_param_count())
+
+
 def solve(instances: Sequence, mode: int = MSP_ALL, time_cap_s: float = 0.0, allow=(MSP_OK,),
-          **opts):
+          order: int = MSP_PLAIN, scorer=None, **opts):
     """Build, reduce and enumerate a batch of instances (objects with .A and
     .d); returns (Result, [solutions per instance], Context)."""
     from .instances import pack
     pk = pack(list(instances))
     ctx = Context(**opts)
+    if scorer is not None:
+        ctx.msp_set_scorer(scorer)
     ctx.msp_build_lattice(pk.dims, pk.A, pk.d)
     ctx.msp_reduce()
-    res = ctx.msp_enumerate(mode, MSP_PLAIN, time_cap_s, allow=allow)
+    res = ctx.msp_enumerate(mode, order, time_cap_s, allow=allow)
     sols = [ctx.msp_solutions(i) for i in range(len(pk.dims))]
     return res, sols, ctx
