@@ -168,6 +168,20 @@ MSP_API msp_status msp_enumerate(msp_ctx *ctx, int mode, int order, double time_
  * msp_wait(). */
 MSP_API msp_status msp_run_async(msp_ctx *ctx, int mode, int order);
 
+/* Capture one whole step of the current batch -- lattice rebuilt from the
+ * stored A and d, reduction, split, order, enumeration, solution collection
+ * -- into a CUDA graph owned by the context.  Requires one completed
+ * enumeration of the batch first (so every buffer exists); replaces any
+ * previous graph.  msp_graph_launch() replays it on the context's stream
+ * without host work between the kernels; read results with msp_wait().
+ * The graph reads A and d from the context's device copies, so a later
+ * msp_build_lattice() with a batch of the same layout (same count and same
+ * (m, n) per instance) keeps it valid and the next replay solves the new
+ * batch; a different layout discards it (msp_graph_launch then returns
+ * MSP_ESTATE until the next capture). */
+MSP_API msp_status msp_graph_capture(msp_ctx *ctx, int mode, int order);
+MSP_API msp_status msp_graph_launch(msp_ctx *ctx);
+
 /* Synchronise and read the statistics of the last msp_run_async(). */
 MSP_API msp_status msp_wait(msp_ctx *ctx, msp_stats *stats, msp_stats *total);
 

@@ -50,6 +50,15 @@
  *         |w|_1: G interleaved partial sums s_l = sum_{c = l mod G} |w_c|
  *               (ascending c), then pairwise s_l += s_{l+off}, off = G/2..1.
  *       G ("lanes") is a parameter; G = 1 is the sequential sum.
+ *   R10 Limited discrepancy search (Sec. 3, after Harvey and Ginsberg): a
+ *       discrepancy is a level where u_t differs from the heuristic first
+ *       value u^1 of that level's walk (the rounded centre; 0 on the
+ *       all-zero levels of sym mode), whatever its rank in the zig-zag.
+ *       Iteration k walks Algorithm 1 but tries a value other than u^1 only
+ *       while the path above carries fewer than k discrepancies, and reports
+ *       a leaf only when its path carries exactly k, so iterations
+ *       k = 0, 1, 2, ... report every solution exactly once.  Nodes are
+ *       counted as in R8 (the nodes of lower discrepancy are visited again).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (see oracle/build.py).
  */
@@ -306,12 +315,15 @@ typedef struct {
                         /* of descending (top-k split); -1: off                 */
     int sub_level;      /* >= 0: enumerate only the subtree below a prefix whose */
                         /* values u[sub_level+1 .. dd-1] are given; -1: off       */
+    int lds;            /* >= 0: one limited-discrepancy iteration with this     */
+                        /* budget (R10); -1: plain depth-first search            */
 } oracle_enum_opts;
 
 typedef struct {
     int64_t nodes, passed, leaves;
     int64_t nsol;       /* number of solutions found (may exceed sol_cap) */
     int64_t nprefix;    /* number of split prefixes found (may exceed cap) */
+    int64_t lds_cuts;   /* values not tried because of the discrepancy budget */
     int stopped;
 } oracle_enum_stats;
 
@@ -385,7 +397,7 @@ static int leaf_check(enum_state *e)
 }
 
 /* enum(t, w') of Algorithm 1.  wp = w^{(t+1)}, rho_p = ||w^{(t+1)}||^2. */
-static void enum_level(enum_state *e, int t, const double *wp, double rho_p)
+static void enum_level(enum_state *e, int t, const double *wp, double rho_p, int disc)
 {
     const int dd = e->dd, dim = e->dim;
     double w[dim];
@@ -404,6 +416,10 @@ static void enum_level(enum_state *e, int t, const double *wp, double rho_p)
     long u = u1;
 
     for (;;) {
+        if (e->o.lds >= 0 && u != u1 && disc + 1 > e->o.lds) {   /* budget spent (R10) */
+            e->s.lds_cuts++;
+            return;
+        }
         e->u[t] = (int32_t)u;
         const double x = (double)u + y;            /* sum_{i>=t} u_i mu_it */
         const double xx = x * x;
@@ -435,13 +451,13 @@ static void enum_level(enum_state *e, int t, const double *wp, double rho_p)
                         e->pre_rho[p] = rho;
                     }
                 } else {
-                    enum_level(e, t - 1, w, rho);  /* step forward */
+                    enum_level(e, t - 1, w, rho, disc + (u != u1));  /* step forward */
                     if (e->s.stopped) return;
                 }
             }
         } else {
             e->s.leaves++;
-            if (leaf_check(e)) {
+            if ((e->o.lds < 0 || disc + (u != u1) == e->o.lds) && leaf_check(e)) {
                 int64_t q = e->s.nsol++;
                 if (q < e->sol_cap) memcpy(e->sol + (size_t)q * e->n, e->xbuf, (size_t)e->n);
                 if (e->o.first) { e->s.stopped = 1; return; }
@@ -485,11 +501,16 @@ int oracle_enumerate(int dd, int dim, const double *mu, const double *B, const d
     }
     int top = dd - 1;
     double rho0 = 0.0;
+    int disc0 = 0;
     if (o->sub_level >= 0) {
         if (o->sub_level >= dd - 1) { free(e.u); free(e.vbuf); free(e.xbuf); free(w0); return OR_EINVAL; }
+        int zero_prefix = 1;
         for (int t = dd - 1; t > o->sub_level; --t) {
             e.u[t] = prefix_u[t];
             const double y = center(&e, t);
+            const long first = (zero_prefix && o->sym) ? 0 : (long)rint(-y);   /* u^1 of level t */
+            disc0 += (e.u[t] != first);
+            zero_prefix = zero_prefix && (e.u[t] == 0);
             const double x = (double)e.u[t] + y;
             const double xx = x * x;
             rho0 = fma(xx, B[t], rho0);
@@ -497,7 +518,7 @@ int oracle_enumerate(int dd, int dim, const double *mu, const double *B, const d
         }
         top = o->sub_level;
     }
-    enum_level(&e, top, w0, rho0);
+    enum_level(&e, top, w0, rho0, disc0);
     *out = e.s;
     free(e.u); free(e.vbuf); free(e.xbuf); free(w0);
     return OR_OK;

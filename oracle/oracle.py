@@ -33,12 +33,13 @@ class OracleError(RuntimeError):
 class _EnumOpts(C.Structure):
     _fields_ = [("hoelder", C.c_int), ("sym", C.c_int), ("lanes", C.c_int),
                 ("use_eps", C.c_int), ("first", C.c_int), ("split_level", C.c_int),
-                ("sub_level", C.c_int)]
+                ("sub_level", C.c_int), ("lds", C.c_int)]
 
 
 class _EnumStats(C.Structure):
     _fields_ = [("nodes", C.c_int64), ("passed", C.c_int64), ("leaves", C.c_int64),
-                ("nsol", C.c_int64), ("nprefix", C.c_int64), ("stopped", C.c_int)]
+                ("nsol", C.c_int64), ("nprefix", C.c_int64), ("lds_cuts", C.c_int64),
+                ("stopped", C.c_int)]
 
 
 _lib = None
@@ -139,6 +140,7 @@ class EnumResult:
     prefix_rho: Optional[np.ndarray] = None
     nprefix: int = 0
     stopped: bool = False
+    lds_cuts: int = 0
 
 
 def sort_solutions(x: np.ndarray) -> np.ndarray:
@@ -152,16 +154,17 @@ def enumerate(kern: np.ndarray, g: GSO, A: np.ndarray, d: np.ndarray, *,
               hoelder: int = HOELDER_CUT, sym: bool = True, lanes: int = 32,
               use_eps: bool = True, first: bool = False,
               split_level: int = -1, sub_level: int = -1,
-              prefix: Optional[np.ndarray] = None,
+              prefix: Optional[np.ndarray] = None, lds: int = -1,
               sol_cap: int = 1 << 16, prefix_cap: int = 1 << 20) -> EnumResult:
     """Algorithm 1 over the whole tree, the top part down to ``split_level``
-    (recording prefixes), or the subtree below ``prefix`` at ``sub_level``."""
+    (recording prefixes), or the subtree below ``prefix`` at ``sub_level``.
+    ``lds`` >= 0 runs one limited-discrepancy iteration with that budget."""
     kb = np.ascontiguousarray(kern, dtype=np.int32)
     A = np.ascontiguousarray(A, dtype=np.int32)
     d = np.ascontiguousarray(d, dtype=np.int64)
     dd, dim = kb.shape
     m, n = A.shape
-    o = _EnumOpts(hoelder, int(sym), lanes, int(use_eps), int(first), split_level, sub_level)
+    o = _EnumOpts(hoelder, int(sym), lanes, int(use_eps), int(first), split_level, sub_level, lds)
     pu = np.ascontiguousarray(prefix if prefix is not None else np.zeros(dd), dtype=np.int32)
     sol = np.zeros((sol_cap, max(n, 1)), np.uint8)
     pcap = prefix_cap if split_level >= 0 else 0
@@ -178,11 +181,25 @@ def enumerate(kern: np.ndarray, g: GSO, A: np.ndarray, d: np.ndarray, *,
         raise OracleError(f"enumerate: {st.nprefix} prefixes exceed prefix_cap={pcap}")
     res = EnumResult(nodes=st.nodes, passed=st.passed, leaves=st.leaves,
                      solutions=sort_solutions(sol[:st.nsol].copy()), nsol=int(st.nsol),
-                     nprefix=int(st.nprefix), stopped=bool(st.stopped))
+                     nprefix=int(st.nprefix), stopped=bool(st.stopped), lds_cuts=int(st.lds_cuts))
     if pcap:
         res.prefixes = pre_u[:st.nprefix].copy()
         res.prefix_rho = pre_rho[:st.nprefix].copy()
     return res
+
+
+def enumerate_lds(kern: np.ndarray, g: GSO, A: np.ndarray, d: np.ndarray, *, first: bool = False,
+                  max_budget: int = 1 << 20, **kw) -> list:
+    """Limited discrepancy search: iterations k = 0, 1, 2, ... until one
+    reports a solution (first) or no value was held back by the budget (the
+    tree is exhausted).  Returns the per-iteration results."""
+    out = []
+    for k in range(max_budget + 1):
+        r = enumerate(kern, g, A, d, first=first, lds=k, **kw)
+        out.append(r)
+        if (first and r.nsol > 0) or r.lds_cuts == 0:
+            break
+    return out
 
 
 @dataclass

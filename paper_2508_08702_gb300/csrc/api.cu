@@ -66,6 +66,7 @@ struct msp_ctx {
     int count = 0, Kmax = 0, dimMax = 0, dimPad = 0;
     int64_t F = 0;
     std::vector<InstDesc> hinst;
+    std::vector<InstDesc> layout;        // descriptors as msp_build_lattice wrote them
     std::vector<msp_stats> stats;
     int last_mode = 0;
     double last_ms = 0.0;
@@ -77,7 +78,14 @@ struct msp_ctx {
     // device buffers
     Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, bq, nbq, fu, fdisc, fxsum, frho, fw, fcnt, qbase, sols, ctrl, soff,
         fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_seq, feat, prof, yout, skeys, svals, skeys2,
-        svals2, perm, theta, mlpwork;
+        svals2, perm, theta, mlpwork, inst0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cst = nullptr;          // private stream the step is captured on
+    int graph_mode = 0;
+    int64_t graph_launches = 0;
+    Pools graph_P{};                     // buffers and layout the graph was captured on
+    std::vector<InstDesc> graph_inst;
     bool scorer_set = false;
     bool features_valid = false;
     std::vector<int64_t> soff_h;
@@ -95,6 +103,24 @@ msp_status fail(msp_ctx* c, msp_status s, const std::string& what) {
 
 msp_status cuda_fail(msp_ctx* c, cudaError_t e, const char* where) {
     return fail(c, MSP_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Event record that also times a graph replay: inside a capture the record
+// becomes a graph node (external record) instead of a capture-internal marker.
+void record(msp_ctx* c, cudaEvent_t ev) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, c->st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, c->st);
+}
+
+void drop_graph(msp_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->graph_inst.clear();
 }
 
 msp_status ensure(msp_ctx* c, Buf& b, size_t bytes, const char* name) {
@@ -267,7 +293,10 @@ void msp_destroy(msp_ctx* c) {
                   &c->bhat, &c->bq, &c->nbq, &c->fdisc, &c->fxsum, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
                   &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols, &c->don,
                   &c->don_seq, &c->feat, &c->prof, &c->yout, &c->skeys, &c->svals, &c->skeys2, &c->svals2,
-                  &c->perm, &c->theta, &c->mlpwork};
+                  &c->perm, &c->theta, &c->mlpwork, &c->inst0};
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->cst) cudaStreamDestroy(c->cst);
     for (Buf* b : all)
         if (b->p) cudaFree(b->p);
     for (cudaEvent_t ev : {c->ev0, c->ev1, c->evr0, c->evr1, c->evs1, c->eve1})
@@ -321,6 +350,7 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
 #define ENSURE(buf, bytes)                                               \
     if ((s = ensure(c, c->buf, (size_t)(bytes), #buf)) != MSP_OK) return s;
     ENSURE(inst, sizeof(InstDesc) * count);
+    ENSURE(inst0, sizeof(InstDesc) * count);
     ENSURE(cnt, sizeof(InstCounters) * count);
     ENSURE(A, sizeof(int32_t) * nA);
     ENSURE(d, sizeof(int64_t) * nd);
@@ -370,10 +400,17 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     const cudaMemcpyKind kind = (mem == MSP_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaError_t e = cudaMemcpyAsync(c->A.p, A, sizeof(int32_t) * nA, kind, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d.p, d, sizeof(int64_t) * nd, kind, c->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->inst.p, h.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->inst0.p, h.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->inst.p, c->inst0.p, sizeof(InstDesc) * count, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);   // h is a host temporary
     if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt.p, 0, sizeof(InstCounters) * count, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "msp_build_lattice copies");
     c->hinst = h;
+    c->layout = h;
+    // a captured step stays valid for new A, d of the same layout in the same buffers
+    if (c->gexec && (std::memcmp(&c->graph_P, &c->P, sizeof(Pools)) != 0 || c->graph_inst.size() != h.size() ||
+                     std::memcmp(c->graph_inst.data(), h.data(), sizeof(InstDesc) * h.size()) != 0))
+        drop_graph(c);
     build_lattice_kernel<<<count, 128, 0, c->st>>>(c->P, c->o.N);
     ++c->launches;
     if ((s = check_launch(c, "build_lattice_kernel")) != MSP_OK) return s;
@@ -385,7 +422,7 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
 msp_status msp_reduce(msp_ctx* c) {
     if (!c) return MSP_EINVAL;
     if (c->state < 1) return fail(c, MSP_ESTATE, "msp_reduce before msp_build_lattice");
-    cudaEventRecord(c->evr0, c->st);
+    record(c, c->evr0);
     lll_kernel<<<c->count, 32, 0, c->st>>>(c->P, c->o.delta, c->o.eta, c->o.lll_max_iter,
                                            (unsigned long long)(c->o.max_seconds * 1e9));
     ++c->launches;
@@ -397,7 +434,7 @@ msp_status msp_reduce(msp_ctx* c) {
     prep_fixed_kernel<<<c->count, 32, 0, c->st>>>(c->P, c->o.use_eps, c->dimPad);
     ++c->launches;
     if ((s = check_launch(c, "prep_fixed_kernel")) != MSP_OK) return s;
-    cudaEventRecord(c->evr1, c->st);
+    record(c, c->evr1);
     c->reduce_timed = true;
     c->state = 2;
     return MSP_OK;
@@ -421,7 +458,7 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
     // the caller's cap, else the context's safety cap: no walk outlives it
     const double cap_s = time_cap_s > 0 ? std::min(time_cap_s, c->o.max_seconds) : c->o.max_seconds;
     const unsigned long long cap_ns = (unsigned long long)(cap_s * 1e9);
-    cudaEventRecord(c->ev0, c->st);
+    record(c, c->ev0);
     if ((e = launch_start(ptr<Ctrl>(c->ctrl), cap_ns, c->st)) != cudaSuccess) return cuda_fail(c, e, "start");
     ++c->launches;
     if ((e = launch_split(c->P, cfg, c->o.lanes, c->o.split_depth, target, ptr<int64_t>(c->fcnt), c->st)) !=
@@ -458,17 +495,17 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
             return cuda_fail(c, e, "order");
         Pq.qperm = ptr<int64_t>(c->perm);
     }
-    cudaEventRecord(c->evs1, c->st);
+    record(c, c->evs1);
     if ((e = launch_enum(Pq, cfg, c->o.lanes, blocks, threads, ptr<char>(c->scratch), c->Kmax, c->dimPad, c->st)) !=
         cudaSuccess)
         return cuda_fail(c, e, "enumerate");
     ++c->launches;
-    cudaEventRecord(c->eve1, c->st);
+    record(c, c->eve1);
     if ((e = launch_collect(c->P, ptr<int64_t>(c->soff), ptr<unsigned long long>(c->fill), ptr<SolRec>(c->seg),
                             ptr<SolRec>(c->sout), c->st)) != cudaSuccess)
         return cuda_fail(c, e, "collect");
     c->launches += 4;
-    cudaEventRecord(c->ev1, c->st);
+    record(c, c->ev1);
     c->last_mode = mode;
     c->state = 3;
     c->sout_valid = false;
@@ -482,6 +519,65 @@ msp_status msp_run_async(msp_ctx* c, int mode, int order) {
     msp_status s = msp_reduce(c);
     if (s != MSP_OK) return s;
     return queue_enumerate(c, mode, order, 0.0);
+}
+
+// One whole step on the device-resident batch: descriptors reset from the
+// pristine copy, lattice rebuilt from the stored A and d, reduction, split,
+// order, enumeration, collection.  No host synchronisation inside.
+static msp_status queue_step(msp_ctx* c, int mode, int order) {
+    cudaError_t e = cudaMemcpyAsync(c->inst.p, c->inst0.p, sizeof(InstDesc) * c->count, cudaMemcpyDeviceToDevice, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reset descriptors");
+    build_lattice_kernel<<<c->count, 128, 0, c->st>>>(c->P, c->o.N);
+    ++c->launches;
+    msp_status s = check_launch(c, "build_lattice_kernel");
+    if (s != MSP_OK) return s;
+    if ((s = msp_reduce(c)) != MSP_OK) return s;
+    return queue_enumerate(c, mode, order, 0.0);
+}
+
+msp_status msp_graph_capture(msp_ctx* c, int mode, int order) {
+    if (!c) return MSP_EINVAL;
+    if (c->state < 3) return fail(c, MSP_ESTATE, "msp_graph_capture: run one enumeration of the batch first");
+    if (mode != MSP_ALL && mode != MSP_FIRST) return fail(c, MSP_EINVAL, "bad mode");
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msp_graph_capture sync");
+    drop_graph(c);
+    // the caller's stream may be the legacy default stream, which cannot be
+    // captured: capture on a private stream, replay on the caller's
+    if (!c->cst && (e = cudaStreamCreateWithFlags(&c->cst, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(c, e, "capture stream");
+    const int64_t launches0 = c->launches;
+    cudaStream_t user = c->st;
+    c->st = c->cst;
+    e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { c->st = user; return cuda_fail(c, e, "cudaStreamBeginCapture"); }
+    msp_status s = queue_step(c, mode, order);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->st, &g);
+    c->st = user;
+    if (s != MSP_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(c, e, "cudaGraphInstantiate"); }
+    c->graph = g;
+    c->graph_P = c->P;
+    c->graph_inst = c->layout;
+    c->graph_launches = c->launches - launches0;
+    c->launches = launches0;
+    c->graph_mode = mode;
+    return MSP_OK;
+}
+
+msp_status msp_graph_launch(msp_ctx* c) {
+    if (!c) return MSP_EINVAL;
+    if (!c->gexec) return fail(c, MSP_ESTATE, "msp_graph_launch before msp_graph_capture");
+    cudaError_t e = cudaGraphLaunch(c->gexec, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+    c->launches += c->graph_launches;
+    c->last_mode = c->graph_mode;
+    c->state = 3;
+    c->sout_valid = false;
+    return MSP_OK;
 }
 
 msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {

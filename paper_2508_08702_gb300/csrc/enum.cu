@@ -1065,8 +1065,13 @@ cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int block
     const int smem = enum_smem_bytes(lanes, threads, Kmax);
 #define MSP_LAUNCH(g, c)                                                                              \
     if (lanes == g && cpl == c) {                                                                     \
-        cudaError_t e = cudaFuncSetAttribute(enum_kernel<g, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
-        if (e != cudaSuccess) return e;                                                               \
+        /* the shared-memory attribute is set once, outside any stream capture */                     \
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;                                     \
+        cudaStreamIsCapturing(st, &cs);                                                               \
+        if (cs == cudaStreamCaptureStatusNone) {                                                      \
+            cudaError_t e = cudaFuncSetAttribute(enum_kernel<g, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+            if (e != cudaSuccess) return e;                                                           \
+        }                                                                                             \
         enum_kernel<g, c><<<blocks, threads, smem, st>>>(P, cfg, scratch, W);                         \
         return cudaGetLastError();                                                                    \
     }

@@ -106,3 +106,50 @@ def first_solution(instances: Sequence, order: int, scorer: Optional[np.ndarray]
                    ph["split"] + ph["enumerate"], res.status)
     ctx.close()
     return out
+
+
+@dataclass
+class OrderWork:
+    plain: List[int]      # per instance: nodes of the subtrees taken before the first one holding a solution
+    learned: List[int]
+    prefixes: List[int]
+
+
+def _work_before_first(nodes: np.ndarray, sols: np.ndarray, order: np.ndarray) -> int:
+    hit = np.nonzero(sols[order] > 0)[0]
+    stop = hit[0] if len(hit) else len(order)
+    return int(nodes[order[:stop]].sum())
+
+
+def sequential_work_to_first(instances: Sequence, scorer: np.ndarray, split_target: int = 0, **opts) -> OrderWork:
+    """Deterministic measure of an order: the nodes a single walker taking
+    the subtrees in that order spends before it reaches the first subtree
+    that holds a solution.  Subtree sizes and outcomes come from one plain
+    all-solutions run (logged per prefix); the learned order ranks the same
+    prefixes by the scorer's priority, ties by depth-first position."""
+    import torch
+    pk = I.pack(list(instances))
+    ctx = M.Context(log_features=1, split_target=split_target, **opts)
+    ctx.msp_build_lattice(pk.dims, pk.A, pk.d)
+    ctx.msp_reduce()
+    ctx.msp_enumerate(M.MSP_ALL, M.MSP_PLAIN)
+    th = torch.from_numpy(np.ascontiguousarray(scorer, dtype=np.float32)).cuda()
+    out = OrderWork([], [], [])
+    for i in range(len(instances)):
+        f = ctx.msp_export_features(i)
+        p = ctx.msp_export_prefixes(i)
+        k = len(f)
+        out.prefixes.append(k)
+        if k == 0:
+            out.plain.append(0)
+            out.learned.append(0)
+            continue
+        y = torch.zeros((k, OUT), dtype=torch.float32, device="cuda")
+        ctx.msp_mlp_forward(th, torch.from_numpy(f).cuda(), y)
+        y = y.cpu().numpy().astype(np.float32)
+        pri = -np.log1p(np.exp(-y[:, 0])) - y[:, 1]
+        learned = np.lexsort((np.arange(k), -pri))
+        out.plain.append(_work_before_first(p["nodes"], p["sols"], np.arange(k)))
+        out.learned.append(_work_before_first(p["nodes"], p["sols"], learned))
+    ctx.close()
+    return out

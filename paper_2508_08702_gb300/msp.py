@@ -93,6 +93,10 @@ def load():
     L.msp_reduce_lattice_noalloc.argtypes = [C.c_int, C.c_int, P, P, C.c_int64, C.c_double, C.c_double,
                                               C.c_int64, P, P]
     L.msp_reduce_lattice_noalloc.restype = C.c_int
+    L.msp_graph_capture.argtypes = [P, C.c_int, C.c_int]
+    L.msp_graph_capture.restype = C.c_int
+    L.msp_graph_launch.argtypes = [P]
+    L.msp_graph_launch.restype = C.c_int
     L.msp_mlp_param_count.argtypes = []
     L.msp_mlp_param_count.restype = C.c_int
     L.msp_set_scorer.argtypes = [P, P]
@@ -222,6 +226,12 @@ class Context:
 
     def msp_run_async(self, mode: int = MSP_ALL, order: int = MSP_PLAIN):
         self._check(self._L.msp_run_async(self._h, mode, order), "msp_run_async")
+
+    def msp_graph_capture(self, mode: int = MSP_ALL, order: int = MSP_PLAIN):
+        self._check(self._L.msp_graph_capture(self._h, mode, order), "msp_graph_capture")
+
+    def msp_graph_launch(self):
+        self._check(self._L.msp_graph_launch(self._h), "msp_graph_launch")
 
     def msp_wait(self, allow=(MSP_OK,)) -> Result:
         stats = (msp_stats * max(self.count, 1))()
