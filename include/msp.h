@@ -56,7 +56,16 @@ typedef enum {
 } msp_status;
 
 typedef enum { MSP_ALL = 0, MSP_FIRST = 1 } msp_mode;      /* all solutions / stop at one  */
-typedef enum { MSP_PLAIN = 0, MSP_LEARNED = 1 } msp_order; /* queue order of the subtrees  */
+/* Order of the search.  PLAIN: depth-first (Algorithm 1) over the subtrees
+ * in depth-first order.  LEARNED: the subtrees ranked by the scorer
+ * (msp_set_scorer); the walk inside a subtree stays depth-first.  LDS:
+ * limited discrepancy search (Sec. 3): iterations k = 0, 1, 2, ... each walk
+ * Algorithm 1 trying a value other than the first of its level (the rounded
+ * centre) only while the path above carries fewer than k such
+ * discrepancies, and report the leaves with exactly k; MSP_FIRST stops an
+ * instance at its first solution, MSP_ALL when an iteration held no value
+ * back (every solution is then reported exactly once). */
+typedef enum { MSP_PLAIN = 0, MSP_LEARNED = 1, MSP_LDS = 2 } msp_order;
 typedef enum { MSP_HOST = 0, MSP_DEVICE = 1 } msp_memory;  /* where A and d live           */
 
 /* Options.  msp_default_opts() fills the defaults given in brackets. */
@@ -87,6 +96,11 @@ typedef struct {
                            /*       hand sibling ranges to idle ones (0: no donation)      */
     int log_features;      /* [0] 1: compute the 32 features of every subtree prefix      */
                            /*     (msp_export_features), e.g. to train the scorer         */
+    int lds_budget;        /* [-1] MSP_LDS: >= 0 runs only the iteration with this budget */
+    int lds_max;           /* [127] MSP_LDS: last budget tried (at most 127; 127 always   */
+                           /*       exhausts a tree, whose paths have at most 127 levels) */
+    int first_split_target; /* [16384] split target of MSP_FIRST when split_target = 0: */
+                           /*       small subtrees let a good queue order pay off        */
 } msp_opts;
 
 /* Per-instance results of an enumeration. */
@@ -111,7 +125,8 @@ typedef struct {
     double first_ms;       /* MSP_FIRST: device time from the start of the enumeration */
                            /* to this instance's first verified solution (-1: none)   */
     int32_t status;        /* msp_status of this instance                              */
-    int32_t reserved;
+    int32_t lds_budget;    /* MSP_LDS: budget of the iteration that solved (MSP_FIRST) or */
+                           /* finished (MSP_ALL) this instance; -1 otherwise            */
     double ms;             /* wall time of the enumeration call (whole batch)          */
 } msp_stats;
 

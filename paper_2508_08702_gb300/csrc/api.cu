@@ -25,7 +25,7 @@ cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int block
                         int Kmax, int dimPad, cudaStream_t st);
 cudaError_t launch_collect(const Pools& P, int64_t* soff, unsigned long long* fill, SolRec* seg, SolRec* out,
                            cudaStream_t st);
-cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, cudaStream_t st);
+cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, int keep, cudaStream_t st);
 cudaError_t launch_ring_init(unsigned long long* seq, int64_t cap, cudaStream_t st);
 int64_t walker_bytes(int Kmax, int dimPad);
 int64_t donation_slot_bytes(int Kmax, int dimPad);
@@ -78,7 +78,7 @@ struct msp_ctx {
     // device buffers
     Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, bq, nbq, fu, fdisc, fxsum, frho, fw, fcnt, qbase, sols, ctrl, soff,
         fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_seq, feat, prof, yout, skeys, svals, skeys2,
-        svals2, perm, theta, mlpwork, inst0;
+        svals2, perm, theta, mlpwork, inst0, skip;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cst = nullptr;          // private stream the step is captured on
@@ -86,6 +86,8 @@ struct msp_ctx {
     int64_t graph_launches = 0;
     Pools graph_P{};                     // buffers and layout the graph was captured on
     std::vector<InstDesc> graph_inst;
+    std::vector<int32_t> lds_done;       // per instance: budget that solved / finished it (-1)
+    bool last_lds = false;
     bool scorer_set = false;
     bool features_valid = false;
     std::vector<int64_t> soff_h;
@@ -199,6 +201,57 @@ void enum_launch_shape(const msp_ctx* c, int* blocks, int* threads) {
     *blocks = c->sms * bps;
 }
 
+// Buffers whose size follows the per-instance frontier capacity F (prefixes,
+// their logs and features, the sort keys of the queue order).  Grow-only.
+msp_status size_frontier(msp_ctx* c, int64_t F) {
+    const size_t n = (size_t)c->count, K = (size_t)c->Kmax, D = (size_t)c->dimPad;
+    const int64_t cap = (int64_t)n * F;
+    int64_t npad = 1;
+    while (npad < cap) npad <<= 1;
+    msp_status s;
+#define ENSURE(buf, bytes)                                               \
+    if ((s = ensure(c, c->buf, (size_t)(bytes), #buf)) != MSP_OK) return s;
+    ENSURE(fu, sizeof(int32_t) * n * 2 * F * K);
+    ENSURE(frho, sizeof(double) * n * 2 * F);
+    ENSURE(fw, sizeof(double) * n * 2 * F * D);
+    ENSURE(fcnt, sizeof(int64_t) * n * F);
+    ENSURE(fdisc, sizeof(int32_t) * n * 2 * F);
+    ENSURE(fxsum, sizeof(float) * n * 2 * F);
+    ENSURE(plog_nodes, sizeof(int64_t) * n * F);
+    ENSURE(plog_sols, sizeof(int32_t) * n * F);
+    ENSURE(feat, sizeof(float) * 32 * (size_t)cap);
+    ENSURE(yout, sizeof(float) * 8 * (size_t)cap);
+    ENSURE(skeys, sizeof(unsigned long long) * (size_t)npad);
+    ENSURE(svals, sizeof(unsigned long long) * (size_t)npad);
+    ENSURE(skeys2, sizeof(unsigned long long) * (size_t)npad);
+    ENSURE(svals2, sizeof(unsigned long long) * (size_t)npad);
+    ENSURE(perm, sizeof(int64_t) * (size_t)cap);
+#undef ENSURE
+    c->F = F;
+    return MSP_OK;
+}
+
+// Split target of one enumeration: the option, else (first-solution mode) the
+// finer first-solution split, else 8 subtrees per walker over the batch.
+int64_t split_target_of(msp_ctx* c, int mode, int64_t walkers) {
+    if (c->o.split_target > 0) return c->o.split_target;
+    if (mode == MSP_FIRST && c->o.first_split_target > 0) return c->o.first_split_target;
+    return std::max<int64_t>(64, 8 * walkers / std::max(c->count, 1));
+}
+
+// Grows the frontier to 4 x the split target of `mode` (unless the capacity
+// is fixed by an option); a captured graph on the old buffers is dropped.
+msp_status fit_frontier(msp_ctx* c, int mode, int64_t walkers) {
+    if (c->o.split_capacity > 0) return MSP_OK;
+    const int64_t want = 4 * split_target_of(c, mode, walkers);
+    if (want <= c->F) return MSP_OK;
+    msp_status s = size_frontier(c, want);
+    if (s != MSP_OK) return s;
+    refresh_pools(c);
+    if (c->gexec && std::memcmp(&c->graph_P, &c->P, sizeof(Pools)) != 0) drop_graph(c);
+    return MSP_OK;
+}
+
 msp_status check_launch(msp_ctx* c, const char* where) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, where);
@@ -230,6 +283,9 @@ void msp_default_opts(msp_opts* o) {
     o->max_seconds = 600.0;
     o->donation_capacity = 1 << 16;
     o->log_features = 0;
+    o->lds_budget = -1;
+    o->lds_max = 127;
+    o->first_split_target = 16384;
 }
 
 const char* msp_status_string(int s) {
@@ -263,7 +319,8 @@ msp_status msp_create(msp_ctx** out, const msp_opts* opts, void* stream) {
     if (o.N < 1 || o.N > (1LL << 30) || !(o.delta > 0.25 && o.delta < 1.0) || !(o.eta >= 0.5 && o.eta < 1.0) ||
         o.hoelder < 0 || o.hoelder > 2 || (o.lanes != 4 && o.lanes != 8 && o.lanes != 16 && o.lanes != 32) ||
         o.split_depth < 0 || o.warps_per_block < 1 || o.warps_per_block > 8 || o.sol_capacity < 1 ||
-        o.lll_max_iter < 1 || !(o.max_seconds > 0.0) || o.donation_capacity < 0) {
+        o.lll_max_iter < 1 || !(o.max_seconds > 0.0) || o.donation_capacity < 0 || o.lds_budget < -1 ||
+        o.lds_budget > 127 || o.lds_max < 0 || o.lds_max > 127 || o.first_split_target < 0) {
         delete c;
         return MSP_EINVAL;
     }
@@ -293,7 +350,7 @@ void msp_destroy(msp_ctx* c) {
                   &c->bhat, &c->bq, &c->nbq, &c->fdisc, &c->fxsum, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
                   &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols, &c->don,
                   &c->don_seq, &c->feat, &c->prof, &c->yout, &c->skeys, &c->svals, &c->skeys2, &c->svals2,
-                  &c->perm, &c->theta, &c->mlpwork, &c->inst0};
+                  &c->perm, &c->theta, &c->mlpwork, &c->inst0, &c->skip};
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->cst) cudaStreamDestroy(c->cst);
@@ -345,7 +402,7 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     enum_launch_shape(c, &blocks, &threads);
     const int64_t walkers = walkers_of(c, blocks, threads);
     int64_t target = c->o.split_target > 0 ? c->o.split_target : std::max<int64_t>(64, 8 * walkers / count);
-    c->F = c->o.split_capacity > 0 ? std::max<int64_t>(c->o.split_capacity, 1) : 4 * target;
+    const int64_t F = c->o.split_capacity > 0 ? std::max<int64_t>(c->o.split_capacity, 1) : 4 * target;
     msp_status s;
 #define ENSURE(buf, bytes)                                               \
     if ((s = ensure(c, c->buf, (size_t)(bytes), #buf)) != MSP_OK) return s;
@@ -364,14 +421,6 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     ENSURE(bhat, sizeof(double) * nKb);
     ENSURE(bq, sizeof(int32_t) * nBq);
     ENSURE(nbq, sizeof(int64_t) * (size_t)count * Kmax);
-    ENSURE(fu, sizeof(int32_t) * (size_t)count * 2 * c->F * Kmax);
-    ENSURE(frho, sizeof(double) * (size_t)count * 2 * c->F);
-    ENSURE(fw, sizeof(double) * (size_t)count * 2 * c->F * c->dimPad);
-    ENSURE(fcnt, sizeof(int64_t) * (size_t)count * c->F);
-    ENSURE(fdisc, sizeof(int32_t) * (size_t)count * 2 * c->F);
-    ENSURE(fxsum, sizeof(float) * (size_t)count * 2 * c->F);
-    ENSURE(plog_nodes, sizeof(int64_t) * (size_t)count * c->F);
-    ENSURE(plog_sols, sizeof(int32_t) * (size_t)count * c->F);
     ENSURE(don, (size_t)c->o.donation_capacity * donation_slot_bytes(Kmax, c->dimPad));
     ENSURE(don_seq, sizeof(unsigned long long) * (size_t)std::max<int64_t>(c->o.donation_capacity, 1));
     ENSURE(qbase, sizeof(int64_t) * (count + 1));
@@ -382,20 +431,9 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     ENSURE(seg, sizeof(SolRec) * (size_t)c->o.sol_capacity);
     ENSURE(sout, sizeof(SolRec) * (size_t)c->o.sol_capacity);
     ENSURE(scratch, (size_t)walkers * walker_bytes(Kmax, c->dimPad));
-    {
-        const int64_t cap = (int64_t)count * c->F;
-        int64_t npad = 1;
-        while (npad < cap) npad <<= 1;
-        ENSURE(feat, sizeof(float) * 32 * (size_t)cap);
-        ENSURE(prof, sizeof(float) * 17 * (size_t)count);
-        ENSURE(yout, sizeof(float) * 8 * (size_t)cap);
-        ENSURE(skeys, sizeof(unsigned long long) * (size_t)npad);
-        ENSURE(svals, sizeof(unsigned long long) * (size_t)npad);
-        ENSURE(skeys2, sizeof(unsigned long long) * (size_t)npad);
-        ENSURE(svals2, sizeof(unsigned long long) * (size_t)npad);
-        ENSURE(perm, sizeof(int64_t) * (size_t)cap);
-    }
+    ENSURE(prof, sizeof(float) * 17 * (size_t)count);
 #undef ENSURE
+    if ((s = size_frontier(c, F)) != MSP_OK) return s;
     refresh_pools(c);
     const cudaMemcpyKind kind = (mem == MSP_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaError_t e = cudaMemcpyAsync(c->A.p, A, sizeof(int32_t) * nA, kind, c->st);
@@ -440,17 +478,20 @@ msp_status msp_reduce(msp_ctx* c) {
     return MSP_OK;
 }
 
-static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_cap_s) {
-    (void)order;   // the learned order is attached by the scorer module
-    EnumCfg cfg{c->o.hoelder, c->o.sym, c->o.use_eps, mode == MSP_FIRST ? 1 : 0};
+// Queues one enumeration.  lds >= 0: one limited-discrepancy iteration with
+// that budget; cont: a later iteration of the same search (counters, stored
+// solutions, start time and deadline carry over).
+static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_cap_s, int lds = -1,
+                                  bool cont = false) {
+    EnumCfg cfg{c->o.hoelder, c->o.sym, c->o.use_eps, mode == MSP_FIRST ? 1 : 0, lds};
     int blocks, threads;
     enum_launch_shape(c, &blocks, &threads);
     const int64_t walkers = walkers_of(c, blocks, threads);
     msp_status s = ensure(c, c->scratch, (size_t)walkers * walker_bytes(c->Kmax, c->dimPad), "scratch");
     if (s != MSP_OK) return s;
-    int64_t target = c->o.split_target > 0 ? c->o.split_target : std::max<int64_t>(64, 8 * walkers / c->count);
-    target = std::min<int64_t>(target, c->F);
-    cudaError_t e = cudaMemsetAsync(c->cnt.p, 0, sizeof(InstCounters) * c->count, c->st);
+    if ((s = fit_frontier(c, mode, walkers)) != MSP_OK) return s;
+    const int64_t target = std::min<int64_t>(split_target_of(c, mode, walkers), c->F);
+    cudaError_t e = cont ? cudaSuccess : cudaMemsetAsync(c->cnt.p, 0, sizeof(InstCounters) * c->count, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->plog_nodes.p, 0, c->plog_nodes.bytes, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->plog_sols.p, 0, c->plog_sols.bytes, c->st);
     if (e == cudaSuccess && c->o.donation_capacity > 0) e = launch_ring_init(ptr<unsigned long long>(c->don_seq), c->o.donation_capacity, c->st);
@@ -458,10 +499,13 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
     // the caller's cap, else the context's safety cap: no walk outlives it
     const double cap_s = time_cap_s > 0 ? std::min(time_cap_s, c->o.max_seconds) : c->o.max_seconds;
     const unsigned long long cap_ns = (unsigned long long)(cap_s * 1e9);
-    record(c, c->ev0);
-    if ((e = launch_start(ptr<Ctrl>(c->ctrl), cap_ns, c->st)) != cudaSuccess) return cuda_fail(c, e, "start");
+    if (!cont) record(c, c->ev0);
+    if ((e = launch_start(ptr<Ctrl>(c->ctrl), cap_ns, cont ? 1 : 0, c->st)) != cudaSuccess)
+        return cuda_fail(c, e, "start");
     ++c->launches;
-    if ((e = launch_split(c->P, cfg, c->o.lanes, c->o.split_depth, target, ptr<int64_t>(c->fcnt), c->st)) !=
+    Pools Ps = c->P;
+    Ps.skip = lds >= 0 ? ptr<unsigned char>(c->skip) : nullptr;
+    if ((e = launch_split(Ps, cfg, c->o.lanes, c->o.split_depth, target, ptr<int64_t>(c->fcnt), c->st)) !=
         cudaSuccess)
         return cuda_fail(c, e, "split");
     c->launches += 2;
@@ -495,7 +539,7 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
             return cuda_fail(c, e, "order");
         Pq.qperm = ptr<int64_t>(c->perm);
     }
-    record(c, c->evs1);
+    if (!cont) record(c, c->evs1);
     if ((e = launch_enum(Pq, cfg, c->o.lanes, blocks, threads, ptr<char>(c->scratch), c->Kmax, c->dimPad, c->st)) !=
         cudaSuccess)
         return cuda_fail(c, e, "enumerate");
@@ -507,8 +551,56 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
     c->launches += 4;
     record(c, c->ev1);
     c->last_mode = mode;
+    c->last_lds = lds >= 0;
     c->state = 3;
     c->sout_valid = false;
+    return MSP_OK;
+}
+
+// Limited discrepancy search (Sec. 3): iterations with budgets 0, 1, 2, ...
+// (or the one budget of opts.lds_budget).  Between iterations the host reads
+// the per-instance counters: an instance is finished once it has a solution
+// (MSP_FIRST) or once an iteration held no value back for want of budget
+// (its tree is exhausted); finished instances get no subtrees afterwards.
+static msp_status run_lds(msp_ctx* c, int mode, double time_cap_s) {
+    const int n = c->count;
+    msp_status s = ensure(c, c->skip, (size_t)n, "skip");
+    if (s != MSP_OK) return s;
+    std::vector<unsigned char> skip(n, 0);
+    std::vector<unsigned long long> cuts_seen(n, 0);
+    std::vector<InstCounters> cn(n);
+    std::vector<InstDesc> h(n);
+    c->lds_done.assign(n, -1);
+    const int k0 = c->o.lds_budget >= 0 ? c->o.lds_budget : 0;
+    const int k1 = c->o.lds_budget >= 0 ? c->o.lds_budget : c->o.lds_max;
+    cudaError_t e = cudaMemsetAsync(c->skip.p, 0, (size_t)n, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lds skip");
+    for (int k = k0; k <= k1; ++k) {
+        if ((s = queue_enumerate(c, mode, MSP_LDS, time_cap_s, k, k != k0)) != MSP_OK) return s;
+        Ctrl ctl;
+        e = cudaStreamSynchronize(c->st);
+        if (e == cudaSuccess) e = cudaMemcpy(cn.data(), c->cnt.p, sizeof(InstCounters) * n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(h.data(), c->inst.p, sizeof(InstDesc) * n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&ctl, c->ctrl.p, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lds iteration");
+        bool all_done = true;
+        for (int i = 0; i < n; ++i) {
+            if (skip[i]) continue;
+            const unsigned long long cuts = cn[i].lds_cuts - cuts_seen[i];
+            cuts_seen[i] = cn[i].lds_cuts;
+            const bool finished = h[i].status != ST_OK || (mode == MSP_FIRST && cn[i].nsol > 0) || cuts == 0;
+            if (finished) {
+                skip[i] = 1;
+                c->lds_done[i] = k;
+            } else {
+                all_done = false;
+            }
+        }
+        if (all_done || ctl.stop == 2 || k == k1) break;
+        e = cudaMemcpyAsync(c->skip.p, skip.data(), (size_t)n, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);   // skip is a host temporary
+        if (e != cudaSuccess) return cuda_fail(c, e, "lds skip");
+    }
     return MSP_OK;
 }
 
@@ -516,6 +608,8 @@ msp_status msp_run_async(msp_ctx* c, int mode, int order) {
     if (!c) return MSP_EINVAL;
     if (c->state < 1) return fail(c, MSP_ESTATE, "msp_run_async before msp_build_lattice");
     if (mode != MSP_ALL && mode != MSP_FIRST) return fail(c, MSP_EINVAL, "bad mode");
+    if (order != MSP_PLAIN && order != MSP_LEARNED)
+        return fail(c, MSP_EINVAL, "msp_run_async: order must be MSP_PLAIN or MSP_LEARNED (MSP_LDS: msp_enumerate)");
     msp_status s = msp_reduce(c);
     if (s != MSP_OK) return s;
     return queue_enumerate(c, mode, order, 0.0);
@@ -539,9 +633,17 @@ msp_status msp_graph_capture(msp_ctx* c, int mode, int order) {
     if (!c) return MSP_EINVAL;
     if (c->state < 3) return fail(c, MSP_ESTATE, "msp_graph_capture: run one enumeration of the batch first");
     if (mode != MSP_ALL && mode != MSP_FIRST) return fail(c, MSP_EINVAL, "bad mode");
+    if (order != MSP_PLAIN && order != MSP_LEARNED)
+        return fail(c, MSP_EINVAL, "msp_graph_capture: order must be MSP_PLAIN or MSP_LEARNED");
     cudaError_t e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "msp_graph_capture sync");
     drop_graph(c);
+    {   // every buffer the step touches exists before the capture starts
+        int blocks, threads;
+        enum_launch_shape(c, &blocks, &threads);
+        msp_status s0 = fit_frontier(c, mode, walkers_of(c, blocks, threads));
+        if (s0 != MSP_OK) return s0;
+    }
     // the caller's stream may be the legacy default stream, which cannot be
     // captured: capture on a private stream, replay on the caller's
     if (!c->cst && (e = cudaStreamCreateWithFlags(&c->cst, cudaStreamNonBlocking)) != cudaSuccess)
@@ -619,6 +721,7 @@ msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {
         S.center_fma = (int64_t)cn[i].center_fma;
         S.fallbacks = (int64_t)cn[i].fallbacks;
         S.first_ms = (c->last_mode == MSP_FIRST && cn[i].nsol > 0) ? (double)cn[i].first_ns * 1e-6 : -1.0;
+        S.lds_budget = (c->last_lds && i < (int)c->lds_done.size()) ? c->lds_done[i] : -1;
         int32_t st = h[i].status;
         if (st == MSP_OK && ctl.stop == 2) st = MSP_ETIMEOUT;
         if (st == MSP_OK && trunc) st = MSP_ETRUNC;
@@ -650,8 +753,8 @@ msp_status msp_enumerate(msp_ctx* c, int mode, int order, double time_cap_s, msp
     if (!c) return MSP_EINVAL;
     if (c->state < 2) return fail(c, MSP_ESTATE, "msp_enumerate before msp_reduce");
     if (mode != MSP_ALL && mode != MSP_FIRST) return fail(c, MSP_EINVAL, "bad mode");
-    if (order != MSP_PLAIN && order != MSP_LEARNED) return fail(c, MSP_EINVAL, "bad order");
-    msp_status s = queue_enumerate(c, mode, order, time_cap_s);
+    if (order != MSP_PLAIN && order != MSP_LEARNED && order != MSP_LDS) return fail(c, MSP_EINVAL, "bad order");
+    msp_status s = order == MSP_LDS ? run_lds(c, mode, time_cap_s) : queue_enumerate(c, mode, order, time_cap_s);
     if (s != MSP_OK) return s;
     return msp_wait(c, stats, total);
 }

@@ -49,6 +49,7 @@ struct InstCounters {
     unsigned long long center_fma;                  // centre-fold fmas of the walkers
     unsigned long long fallbacks;                   // Hoelder tests decided by the FP64 rebuild
     unsigned long long first_ns;                    // first-solution mode: time of the first solution
+    unsigned long long lds_cuts;                    // values held back by the discrepancy budget
 };
 
 // A found solution: x_c is bit (127 - c) of the 128-bit key (hi:lo), so that
@@ -96,6 +97,7 @@ struct Pools {
     SolRec* sols;
     int64_t sol_cap;
     struct Ctrl* ctrl;
+    const unsigned char* skip;         // optional, per instance: 1 = no subtrees in this launch
 };
 
 // Control words of one enumeration, in device memory.
@@ -122,6 +124,7 @@ struct EnumCfg {
     int sym;         // 1: one of v, -v;  0: both signs
     int use_eps;     // slack eps = (n+1) 2^-20 on both tests
     int first;       // stop at the first solution
+    int lds;         // >= 0: one limited-discrepancy iteration with this budget; -1: depth-first
 };
 
 __device__ __forceinline__ int64_t frontier_index(const Pools& P, int inst, int sel, int64_t j) {

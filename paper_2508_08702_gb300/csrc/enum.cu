@@ -20,6 +20,10 @@
 //   zig-zag value, then walk only in that direction; second failure or a
 //   norm failure: step back.
 //   t = 0: exact integer check of v = sum_j u_j b_j (Theorem 1).
+// Limited discrepancy search (Sec. 3): a value other than the first of its
+// level's walk (u^1, the rounded centre) is a discrepancy; an iteration with
+// budget k tries such a value only while the path above carries fewer than
+// k of them and reports a leaf only when its path carries exactly k.
 // The centre uses the partial-sum cache of Gama-Nguyen-Regev: sigma[t][i]
 // holds the fold down to index i, J[t] the highest level changed since, so
 // only the changed tail of the fold is redone -- the same operations in
@@ -49,7 +53,7 @@ template <int G, bool WRITE>
 __device__ int64_t expand_parent(const Pools& P, const EnumCfg& cfg, int inst, int dd, int dim, int t,
                                  const int32_t* __restrict__ pu, double prho, const double* __restrict__ pw,
                                  int pdisc, float pxsum, int out_sel, int64_t base, unsigned long long& nodes,
-                                 unsigned long long& passed, bool& ovf) {
+                                 unsigned long long& passed, unsigned long long& cuts, bool& ovf) {
     const InstDesc& I = P.inst[inst];
     const double* muT = P.muT + I.offMuT;
     const double* Bt = P.B + I.offB;
@@ -74,6 +78,10 @@ __device__ int64_t expand_parent(const Pools& P, const EnumCfg& cfg, int inst, i
     int u = u1;
     int64_t nch = 0;
     for (;;) {
+        if (cfg.lds >= 0 && u != u1 && pdisc >= cfg.lds) {   // discrepancy budget spent
+            if (WRITE) ++cuts;
+            break;
+        }
         if (u >= kUMax || u <= -kUMax) { ovf = true; break; }
         const double x = __dadd_rn((double)u, y);
         const double rho = __fma_rn(__dmul_rn(x, x), Bt[t], prho);
@@ -154,7 +162,7 @@ __global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int ma
     const int inst = blockIdx.x;
     InstDesc& I = P.inst[inst];
     __shared__ int s_ok;
-    if (threadIdx.x == 0) s_ok = (I.status == ST_OK);
+    if (threadIdx.x == 0) s_ok = (I.status == ST_OK) && !(P.skip && P.skip[inst]);
     __syncthreads();
     if (!s_ok) {
         if (threadIdx.x == 0) { I.nprefix = 0; I.split_level = 0; I.front_sel = 0; }
@@ -172,15 +180,15 @@ __global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int ma
     __syncthreads();
     int sel = 0, t = dd - 1, depth = 0;
     int64_t count = 1;
-    unsigned long long nodes = 0, passed = 0;
+    unsigned long long nodes = 0, passed = 0, cuts = 0;
     bool ovf = false;
     __shared__ int s_ovf;
     while (depth < max_depth && t >= 1 && count < target) {
         for (int64_t p = threadIdx.x; p < count; p += blockDim.x) {
             const int64_t o = frontier_index(P, inst, sel, p);
-            unsigned long long dn = 0, dp = 0;
+            unsigned long long dn = 0, dp = 0, dc = 0;
             cnt[p] = expand_parent<G, false>(P, cfg, inst, dd, dim, t, P.fu + o * P.Kmax, P.frho[o],
-                                             P.fw + o * P.dimPad, 0, 0.f, sel ^ 1, 0, dn, dp, ovf);
+                                             P.fw + o * P.dimPad, P.fdisc[o], 0.f, sel ^ 1, 0, dn, dp, dc, ovf);
         }
         if (threadIdx.x == 0) s_ovf = 0;
         __syncthreads();
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int ma
         for (int64_t p = threadIdx.x; p < count; p += blockDim.x) {
             const int64_t o = frontier_index(P, inst, sel, p);
             expand_parent<G, true>(P, cfg, inst, dd, dim, t, P.fu + o * P.Kmax, P.frho[o], P.fw + o * P.dimPad,
-                                   P.fdisc[o], P.fxsum[o], sel ^ 1, cnt[p], nodes, passed, ovf);
+                                   P.fdisc[o], P.fxsum[o], sel ^ 1, cnt[p], nodes, passed, cuts, ovf);
         }
         __syncthreads();
         sel ^= 1;
@@ -209,6 +217,7 @@ __global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int ma
         atomicAdd(&P.cnt[inst].passed, passed);
         atomicAdd(&P.cnt[inst].split_passed, passed);
     }
+    if (cuts) atomicAdd(&P.cnt[inst].lds_cuts, cuts);
     if (threadIdx.x == 0) {
         I.split_level = t + 1;
         I.front_sel = sel;
@@ -217,21 +226,25 @@ __global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int ma
     if (ovf) set_status(I, ST_EOVERFLOW);
 }
 
-// resets the control words and arms the time cap on the device clock
-__global__ void start_kernel(Ctrl* c, unsigned long long cap_ns) {
+// resets the control words and arms the time cap on the device clock;
+// keep != 0 continues a search (the next limited-discrepancy iteration): the
+// start time, the deadline and the stored solutions carry over
+__global__ void start_kernel(Ctrl* c, unsigned long long cap_ns, int keep) {
     c->qhead = 0;
     c->dhead = 0;
     c->dtail = 0;
     c->idle = 0;
     c->busy = 0;
     c->donations = 0;
-    c->walk_cycles = 0;
-    c->life_cycles = 0;
-    c->nsol_total = 0;
     c->stop = 0;
     c->gstatus = 0;
-    c->start_ns = global_time_ns();
-    c->deadline_ns = cap_ns ? c->start_ns + cap_ns : 0ULL;
+    if (!keep) {
+        c->walk_cycles = 0;
+        c->life_cycles = 0;
+        c->nsol_total = 0;
+        c->start_ns = global_time_ns();
+        c->deadline_ns = cap_ns ? c->start_ns + cap_ns : 0ULL;
+    }
     c->solved = 0;
     c->active = 0;
 }
@@ -267,8 +280,9 @@ struct WalkerLayout {
 
 // Level state of one walker in shared memory: for each level t on the
 // current path, the value u being explored there (also as a double), the
-// zig-zag state, the quantised x, the centre y_t and the parent's norm
-// rho_{t+1}.  One base pointer; the arrays follow each other.
+// zig-zag state, the quantised x, the centre y_t, the parent's norm
+// rho_{t+1} and the discrepancies above.  One base pointer; the arrays
+// follow each other.
 struct Levels {
     unsigned char* base;
     int K;
@@ -281,9 +295,11 @@ struct Levels {
     __device__ __forceinline__ short& zi(int t) const { return reinterpret_cast<short*>(base + 32 * K)[t]; }
     __device__ __forceinline__ unsigned char& meta(int t) const { return base[34 * K + t]; }
     __device__ __forceinline__ unsigned char& J(int t) const { return base[35 * K + t]; }
+    // discrepancies on the path above level t (limited discrepancy search)
+    __device__ __forceinline__ unsigned char& dab(int t) const { return base[36 * K + t]; }
 };
 
-__host__ __device__ inline int level_bytes(int Kmax) { return (Kmax * 36 + 15) / 16 * 16; }
+__host__ __device__ inline int level_bytes(int Kmax) { return (Kmax * 37 + 15) / 16 * 16; }
 
 __device__ __forceinline__ Levels levels_at(unsigned char* base, int Kmax) {
     Levels L;
@@ -297,7 +313,7 @@ __device__ __forceinline__ Levels levels_at(unsigned char* base, int Kmax) {
 // slot continues with int32 u[Kmax] (values above t) and the canonical FP64
 // w^(t+1) (double[dimPad]).
 struct DonHdr {
-    int32_t inst, t, u, u1, zi, meta;
+    int32_t inst, t, u, u1, zi, meta, dab, pad;
     int64_t gid;
     double y, rhoP;
 };
@@ -449,12 +465,12 @@ __device__ __noinline__ double canonical_l1(const double* __restrict__ bhat, con
 template <int G>
 __device__ __noinline__ int donate(const Pools& P, int inst, int64_t gid, const Levels& L, const double* root_w,
                                    const double* __restrict__ bhat, int t0, int t, int dd, int dim, int Kmax,
-                                   unsigned gmask) {
+                                   int lds, unsigned gmask) {
     const int lg = threadIdx.x & (G - 1);
     if (P.don_cap <= 0) return 0;
     int h = -1;
-    for (int l = t0; l > t; --l)
-        if (!(L.meta(l) & kDonated)) { h = l; break; }
+    for (int l = t0; l > t; --l)   // untried values of a level are discrepancies: they need budget
+        if (!(L.meta(l) & kDonated) && (lds < 0 || L.dab(l) < lds)) { h = l; break; }
     if (h < 0) return 0;
     // reserve ring index k (slot k mod cap); the slot is free once its
     // sequence number equals k (set by the consumer of index k - cap)
@@ -479,6 +495,7 @@ __device__ __noinline__ int donate(const Pools& P, int inst, int64_t gid, const 
         DonHdr hd;
         hd.inst = inst; hd.t = h; hd.u = L.u(h); hd.u1 = L.u1(h);
         hd.zi = L.zi(h); hd.meta = L.meta(h) & ~kDonated; hd.gid = gid;
+        hd.dab = L.dab(h); hd.pad = 0;
         hd.y = L.y(h); hd.rhoP = L.rho(h);
         *reinterpret_cast<DonHdr*>(sp) = hd;
     }
@@ -562,6 +579,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     const int64_t* nbqtab = nullptr;
     double y = 0.0, rhoP = 0.0, Bt = 0.0;
     int u = 0, u1 = 0, s = 1, zi = 1, dir = 0, act = kEval;
+    int dab = 0;                       // discrepancies on the path above level t
     bool onedir = false, zp = true;
     long long Epar = 0, nbq_t = 0;
     long long W[CPL], T[CPL];
@@ -569,7 +587,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
 #pragma unroll
     for (int q = 0; q < CPL; ++q) { W[q] = 0; T[q] = 0; bq[q] = 0; }
     unsigned long long nodes = 0, passed = 0, cfma = 0;
-    unsigned leaves = 0, fallbacks = 0;
+    unsigned leaves = 0, fallbacks = 0, cuts = 0;
     int item_sols = 0;
     unsigned spins = 0;
     const long long life0 = clock64();
@@ -692,6 +710,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     }
                     for (int c = lg; c < dim; c += G) root_w[c] = P.fw[fo * P.dimPad + c];
                     rhoP = P.frho[fo];
+                    dab = P.fdisc[fo];
                 } else {
                     const char* slot = P.don + id * P.don_stride;
                     const DonHdr hd = *reinterpret_cast<const DonHdr*>(slot);
@@ -715,6 +734,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     s = (hd.meta & kNegS) ? -1 : 1;
                     zp = (hd.meta & kZeroPrefix) != 0;
                     if (onedir) dir = hd.zi; else zi = hd.zi;
+                    dab = hd.dab;
                 }
                 for (int i = lg; i <= t0; i += G) L.J(i) = (unsigned char)(dd - 1);
                 if (lg == 0) L.meta(t0) = 0;
@@ -730,7 +750,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 nbq_t = nbqtab[t];
 #pragma unroll
                 for (int q = 0; q < CPL; ++q) bq[q] = (lg + G * q < dim) ? bqtab[(int64_t)t * dimPad + lg + G * q] : 0;
-                nodes = passed = leaves = cfma = fallbacks = 0;
+                nodes = passed = leaves = cfma = fallbacks = cuts = 0;
                 item_sols = 0;
                 state = kWalk;
                 walk0 = clock64();
@@ -796,7 +816,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 if (__shfl_sync(gmask, st, 0, G)) abort = true;
                 else if (__shfl_sync(gmask, solved, 0, G)) { abort = true; quiet = true; }
                 else if (__shfl_sync(gmask, want, 0, G))
-                    donate<G>(P, inst, gid, L, root_w, bhat, t0, t, dd, dim, Kmax, gmask);
+                    donate<G>(P, inst, gid, L, root_w, bhat, t0, t, dd, dim, Kmax, cfg.lds, gmask);
             }
             if (u >= kUMax || u <= -kUMax) {
                 if (!abort && lg == 0) set_status(P.inst[inst], ST_EOVERFLOW);
@@ -807,16 +827,19 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 // ---- node (t, u): centre, norm (FP64, the canonical operations) ----
                 const double x = __dadd_rn(i2d_exact(u), y);
                 const double rho = __fma_rn(__dmul_rn(x, x), Bt, rhoP);
-                ++nodes;
+                const bool over_budget = cfg.lds >= 0 && u != u1 && dab >= cfg.lds;
+                nodes += over_budget ? 0 : 1;
+                cuts += over_budget ? 1 : 0;
                 long long Ech = 0;
                 int xq = 0;
-                if (__double_as_longlong(rho) > Rbits) {   // norm test on the bit patterns (rho >= 0)
+                if (over_budget || __double_as_longlong(rho) > Rbits) {   // norm test on the bit patterns (rho >= 0)
                     act = kUp;
                 } else {
                     ++passed;
                     if (t == 0) {
                         ++leaves;
-                        item_sols += leaf_check<G, CPL>(P, cfg, inst, L, u, gmask);
+                        if (cfg.lds < 0 || dab + (u != u1 ? 1 : 0) == cfg.lds)
+                            item_sols += leaf_check<G, CPL>(P, cfg, inst, L, u, gmask);
                         act = kNext;
                     } else {
                         // ---- Hoelder test (Theorem 2) through the exact integer filter ----
@@ -871,7 +894,9 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         L.xq(t) = xq;
                         L.y(t) = y;
                         L.rho(t) = rhoP;
+                        L.dab(t) = (unsigned char)dab;
                     }
+                    dab += (u != u1) ? 1 : 0;
 #pragma unroll
                     for (int q = 0; q < CPL; ++q) W[q] = T[q];
                     Epar = Ech;
@@ -910,6 +935,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         if (onedir) dir = L.zi(t); else zi = L.zi(t);
                         y = L.y(t);
                         rhoP = L.rho(t);
+                        dab = L.dab(t);
                         Bt = Btab[t];
                         act = kNext;
                     }
@@ -923,6 +949,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     atomicAdd(&P.cnt[inst].leaves, (unsigned long long)leaves);
                     atomicAdd(&P.cnt[inst].center_fma, cfma);
                     atomicAdd(&P.cnt[inst].fallbacks, (unsigned long long)fallbacks);
+                    if (cuts) atomicAdd(&P.cnt[inst].lds_cuts, (unsigned long long)cuts);
                     atomicAdd(reinterpret_cast<unsigned long long*>(&P.plog_nodes[gid]), nodes);
                     if (item_sols) atomicAdd(&P.plog_sols[gid], item_sols);
                     atomicAdd(&ctrl->walk_cycles, (unsigned long long)(clock64() - walk0));
@@ -1030,8 +1057,8 @@ cudaError_t launch_ring_init(unsigned long long* seq, int64_t cap, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, cudaStream_t st) {
-    start_kernel<<<1, 1, 0, st>>>(ctrl, cap_ns);
+cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, int keep, cudaStream_t st) {
+    start_kernel<<<1, 1, 0, st>>>(ctrl, cap_ns, keep);
     return cudaGetLastError();
 }
 

@@ -108,15 +108,16 @@ __device__ __forceinline__ uint32_t ordered_bits(float x) {   // monotone float 
 }
 
 // stage 1 (learned): key = (instance, descending priority), value = gid.
-// priority = log P(solution) - predicted log(1 + nodes) from the scorer output y
+// priority = the scorer's logit of P(the subtree holds a solution); its
+// node-count output is an auxiliary training target and does not enter the
+// order (discounting by the predicted size found the solution later)
 __global__ void score_keys_kernel(Pools P, const float* __restrict__ y, int64_t npad, unsigned long long* keys,
                                   unsigned long long* vals) {
     const int64_t total = P.qbase[P.count];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
         if (i < total) {
             const int inst = instance_of(P, i);
-            const float z = y[i * 8], ln = y[i * 8 + 1];
-            const float pri = -log1pf(expf(-z)) - ln;
+            const float pri = y[i * 8];
             keys[i] = ((unsigned long long)inst << 32) | (unsigned long long)(~ordered_bits(pri));
             vals[i] = (unsigned long long)i;
         } else {

@@ -27,6 +27,7 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kIn * kHid, kOffW2 = kOffB1 + kHid, 
               kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kOut, kParams = kOffB3 + kOut;   // 6792
 constexpr float kNodeWeight = 0.1f;
 constexpr int kRowsPerBlock = 128;   // 8 warps x 16 rows
+constexpr int kWarps = kRowsPerBlock / 16;
 
 struct __align__(16) MlpSmem {
     __nv_bfloat16 W1T[kHid][kIn + 8];    // [hid][in]   forward layer 1
@@ -45,7 +46,10 @@ struct __align__(16) MlpStage {
     __nv_bfloat16 G1[kRowsPerBlock][kHid];   // dL/d(pre-activation 1)
     __nv_bfloat16 G2[kRowsPerBlock][kHid];   // dL/d(pre-activation 2)
     __nv_bfloat16 GY[kRowsPerBlock][kOut];   // dL/dy
-    float gb1[kHid], gb2[kHid], gb3[kOut];
+    // per-warp partial bias gradients and losses, summed in warp order so
+    // that training is deterministic
+    float gb1w[kWarps][kHid], gb2w[kWarps][kHid], gb3w[kWarps][kOut];
+    float lossw[kWarps];
     float loss;
 };
 
@@ -165,6 +169,17 @@ __global__ void __launch_bounds__(256) mlp_forward_kernel(const float* __restric
     }
 }
 
+// Sum over the 8 row groups g of a warp (lanes 4g + t): every lane gets the
+// column totals of its t, combined in a fixed order.
+__device__ __forceinline__ float2 rows_sum(float a, float b) {
+#pragma unroll
+    for (int off = 4; off <= 16; off <<= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
+    }
+    return make_float2(a, b);
+}
+
 // One block: loss and gradient (summed, already divided by `denom`) over the
 // 128 rows rows[0..127] (row index < 0: padding).  Writes the gradient into
 // grad (kParams floats, accumulated with +=) and adds the loss to *loss.
@@ -172,10 +187,6 @@ __device__ void block_grad(const MlpSmem& S, MlpStage& T, const float* __restric
                            const int64_t* rows, float denom, float pos_weight, float* grad) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int base = warp * 16;
-    for (int e = threadIdx.x; e < kHid; e += blockDim.x) { T.gb1[e] = 0.f; T.gb2[e] = 0.f; }
-    if (threadIdx.x < kOut) T.gb3[threadIdx.x] = 0.f;
-    if (threadIdx.x == 0) T.loss = 0.f;
-    __syncthreads();
     auto x = [&](int r, int c) { const int64_t i = rows[base + r]; return i >= 0 ? X[i * kIn + c] : 0.f; };
     float C1[8][4], C2[8][4], C3[4];
     forward16(S, x, C1, C2, C3);
@@ -215,13 +226,15 @@ __device__ void block_grad(const MlpSmem& S, MlpStage& T, const float* __restric
         }
     }
     for (int off = 16; off >= 1; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
-    if (lane == 0) atomicAdd(&T.loss, lsum);
+    if (lane == 0) T.lossw[warp] = lsum;
     T.GY[base + g][2 * t] = __float2bfloat16_rn(dY[0]);
     T.GY[base + g][2 * t + 1] = __float2bfloat16_rn(dY[1]);
     T.GY[base + g + 8][2 * t] = __float2bfloat16_rn(dY[2]);
     T.GY[base + g + 8][2 * t + 1] = __float2bfloat16_rn(dY[3]);
-    atomicAdd(&T.gb3[2 * t], dY[0] + dY[2]);
-    atomicAdd(&T.gb3[2 * t + 1], dY[1] + dY[3]);
+    {
+        const float2 v = rows_sum(dY[0] + dY[2], dY[1] + dY[3]);
+        if (g == 0) { T.gb3w[warp][2 * t] = v.x; T.gb3w[warp][2 * t + 1] = v.y; }
+    }
     // dH2 = (dY W3^T) * [a2 > 0]   (K = 8 outputs, zero-padded to 16)
     uint32_t ay[4] = {pack_bf16(dY[0], dY[1]), pack_bf16(dY[2], dY[3]), 0u, 0u};
     float D2[8][4];
@@ -232,8 +245,8 @@ __device__ void block_grad(const MlpSmem& S, MlpStage& T, const float* __restric
 #pragma unroll
         for (int q = 0; q < 4; ++q) D2[j][q] = C2[j][q] > 0.f ? D2[j][q] : 0.f;
         const int c = 8 * j + 2 * t;
-        atomicAdd(&T.gb2[c], D2[j][0] + D2[j][2]);
-        atomicAdd(&T.gb2[c + 1], D2[j][1] + D2[j][3]);
+        const float2 v = rows_sum(D2[j][0] + D2[j][2], D2[j][1] + D2[j][3]);
+        if (g == 0) { T.gb2w[warp][c] = v.x; T.gb2w[warp][c + 1] = v.y; }
         T.G2[base + g][c] = __float2bfloat16_rn(D2[j][0]);
         T.G2[base + g][c + 1] = __float2bfloat16_rn(D2[j][1]);
         T.G2[base + g + 8][c] = __float2bfloat16_rn(D2[j][2]);
@@ -257,8 +270,8 @@ __device__ void block_grad(const MlpSmem& S, MlpStage& T, const float* __restric
 #pragma unroll
         for (int q = 0; q < 4; ++q) D1[q] = C1[j][q] > 0.f ? D1[q] : 0.f;
         const int c = 8 * j + 2 * t;
-        atomicAdd(&T.gb1[c], D1[0] + D1[2]);
-        atomicAdd(&T.gb1[c + 1], D1[1] + D1[3]);
+        const float2 v = rows_sum(D1[0] + D1[2], D1[1] + D1[3]);
+        if (g == 0) { T.gb1w[warp][c] = v.x; T.gb1w[warp][c + 1] = v.y; }
         T.G1[base + g][c] = __float2bfloat16_rn(D1[0]);
         T.G1[base + g][c + 1] = __float2bfloat16_rn(D1[1]);
         T.G1[base + g + 8][c] = __float2bfloat16_rn(D1[2]);
@@ -295,10 +308,21 @@ __device__ void block_grad(const MlpSmem& S, MlpStage& T, const float* __restric
         atomicAdd(&grad[off + (r + 8) * ncol + c + 1], D[3]);
     }
     for (int e = threadIdx.x; e < kHid; e += blockDim.x) {
-        atomicAdd(&grad[kOffB1 + e], T.gb1[e]);
-        atomicAdd(&grad[kOffB2 + e], T.gb2[e]);
+        float a = 0.f, b = 0.f;
+        for (int w = 0; w < kWarps; ++w) { a += T.gb1w[w][e]; b += T.gb2w[w][e]; }
+        atomicAdd(&grad[kOffB1 + e], a);
+        atomicAdd(&grad[kOffB2 + e], b);
     }
-    if (threadIdx.x < kOut) atomicAdd(&grad[kOffB3 + threadIdx.x], T.gb3[threadIdx.x]);
+    if (threadIdx.x < kOut) {
+        float a = 0.f;
+        for (int w = 0; w < kWarps; ++w) a += T.gb3w[w][threadIdx.x];
+        atomicAdd(&grad[kOffB3 + threadIdx.x], a);
+    }
+    if (threadIdx.x == 0) {
+        float l = 0.f;
+        for (int w = 0; w < kWarps; ++w) l += T.lossw[w];
+        T.loss = l;
+    }
     __syncthreads();
 }
 

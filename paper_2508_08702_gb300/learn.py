@@ -42,7 +42,7 @@ def init_params(seed: int = 0) -> np.ndarray:
     return theta
 
 
-def collect(instances: Sequence, split_target: int = 0, batch: int = 64, **opts) -> Dataset:
+def collect(instances: Sequence, split_target: int = 16384, batch: int = 64, **opts) -> Dataset:
     """Plain all-solutions runs with feature logging; one row per prefix."""
     xs, ys = [], []
     for b0 in range(0, len(instances), batch):
@@ -112,13 +112,24 @@ def first_solution(instances: Sequence, order: int, scorer: Optional[np.ndarray]
 class OrderWork:
     plain: List[int]      # per instance: nodes of the subtrees taken before the first one holding a solution
     learned: List[int]
+    plain_rank: List[int]     # per instance: queue position of the first subtree holding a solution
+    learned_rank: List[int]
     prefixes: List[int]
 
+    def ratios(self):
+        """Geometric means over the instances with a solution of the learned
+        / plain ratios of (work + 1) and of (rank + 1)."""
+        p, l = np.array(self.plain, float), np.array(self.learned, float)
+        pr, lr = np.array(self.plain_rank, float), np.array(self.learned_rank, float)
+        ok = pr < np.array(self.prefixes)
+        return (float(np.exp(np.mean(np.log((l[ok] + 1) / (p[ok] + 1))))),
+                float(np.exp(np.mean(np.log((lr[ok] + 1) / (pr[ok] + 1))))))
 
-def _work_before_first(nodes: np.ndarray, sols: np.ndarray, order: np.ndarray) -> int:
+
+def _work_before_first(nodes: np.ndarray, sols: np.ndarray, order: np.ndarray):
     hit = np.nonzero(sols[order] > 0)[0]
     stop = hit[0] if len(hit) else len(order)
-    return int(nodes[order[:stop]].sum())
+    return int(nodes[order[:stop]].sum()), int(stop)
 
 
 def sequential_work_to_first(instances: Sequence, scorer: np.ndarray, split_target: int = 0, **opts) -> OrderWork:
@@ -134,22 +145,25 @@ def sequential_work_to_first(instances: Sequence, scorer: np.ndarray, split_targ
     ctx.msp_reduce()
     ctx.msp_enumerate(M.MSP_ALL, M.MSP_PLAIN)
     th = torch.from_numpy(np.ascontiguousarray(scorer, dtype=np.float32)).cuda()
-    out = OrderWork([], [], [])
+    out = OrderWork([], [], [], [], [])
     for i in range(len(instances)):
         f = ctx.msp_export_features(i)
         p = ctx.msp_export_prefixes(i)
         k = len(f)
         out.prefixes.append(k)
         if k == 0:
-            out.plain.append(0)
-            out.learned.append(0)
+            for a in (out.plain, out.learned, out.plain_rank, out.learned_rank):
+                a.append(0)
             continue
         y = torch.zeros((k, OUT), dtype=torch.float32, device="cuda")
         ctx.msp_mlp_forward(th, torch.from_numpy(f).cuda(), y)
-        y = y.cpu().numpy().astype(np.float32)
-        pri = -np.log1p(np.exp(-y[:, 0])) - y[:, 1]
+        pri = y.cpu().numpy()[:, 0]            # the queue priority (logit of P(solution))
         learned = np.lexsort((np.arange(k), -pri))
-        out.plain.append(_work_before_first(p["nodes"], p["sols"], np.arange(k)))
-        out.learned.append(_work_before_first(p["nodes"], p["sols"], learned))
+        w, r = _work_before_first(p["nodes"], p["sols"], np.arange(k))
+        out.plain.append(w)
+        out.plain_rank.append(r)
+        w, r = _work_before_first(p["nodes"], p["sols"], learned)
+        out.learned.append(w)
+        out.learned_rank.append(r)
     ctx.close()
     return out

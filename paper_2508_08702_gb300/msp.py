@@ -19,7 +19,7 @@ from . import build as _build
 MSP_OK, MSP_EINVAL, MSP_ENOMEM, MSP_ECUDA, MSP_EOVERFLOW, MSP_ERANK, MSP_ETIMEOUT, MSP_ETRUNC, \
     MSP_ESTATE, MSP_ECAP, MSP_EQUEUE = range(11)
 MSP_ALL, MSP_FIRST = 0, 1
-MSP_PLAIN, MSP_LEARNED = 0, 1
+MSP_PLAIN, MSP_LEARNED, MSP_LDS = 0, 1, 2
 MSP_HOST, MSP_DEVICE = 0, 1
 
 
@@ -36,7 +36,8 @@ class msp_opts(C.Structure):
                 ("split_target", C.c_int), ("split_capacity", C.c_int),
                 ("warps_per_block", C.c_int), ("blocks_per_sm", C.c_int),
                 ("smem_tables", C.c_int), ("sol_capacity", C.c_int64), ("max_seconds", C.c_double),
-                ("donation_capacity", C.c_int64), ("log_features", C.c_int)]
+                ("donation_capacity", C.c_int64), ("log_features", C.c_int),
+                ("lds_budget", C.c_int), ("lds_max", C.c_int), ("first_split_target", C.c_int)]
 
 
 class msp_stats(C.Structure):
@@ -46,11 +47,11 @@ class msp_stats(C.Structure):
                 ("lll_swaps", C.c_int64), ("split_nodes", C.c_int64), ("split_passed", C.c_int64),
                 ("center_fma", C.c_int64), ("fallbacks", C.c_int64), ("donations", C.c_int64),
                 ("walker_util", C.c_double), ("first_ms", C.c_double), ("status", C.c_int32),
-                ("reserved", C.c_int32),
+                ("lds_budget", C.c_int32),
                 ("ms", C.c_double)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _lib = None

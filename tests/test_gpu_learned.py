@@ -150,18 +150,20 @@ def test_feature_log_is_finite_and_complete():
 
 
 def test_trained_scorer_gains_over_plain_order():
-    """What the network buys: trained on m = 5..7 instances, it orders the
-    subtrees of held-out m = 7 instances (the batch's) so that a walker
-    reaches the first solution-bearing subtree after fewer nodes than in the
-    depth-first order.  All-solutions results are unaffected (tested above)."""
+    """What the network buys: trained on m = 5..7 instances (seeds disjoint
+    from the batch's), it ranks the subtrees of the batch's m = 6, 7
+    instances so that the first subtree holding a solution moves far up the
+    queue, and a walker taking the subtrees in that order spends fewer nodes
+    before reaching it than in the depth-first order (geometric means over
+    the instances; training is deterministic).  All-solutions results are
+    unaffected (tested above)."""
     from paper_2508_08702_gb300 import learn
-    data = learn.collect(I.training_set(128), split_target=2048)
+    data = learn.collect(I.training_set(256), split_target=2048)
     theta, losses = learn.train(data, steps=4000)
-    held = [x for x in I.batch_m4_7(64) if x.m == 7]
+    held = [x for x in I.batch_m4_7(64) if x.m >= 6]
     w = learn.sequential_work_to_first(held, theta, split_target=2048)
-    plain, learned = np.array(w.plain, float), np.array(w.learned, float)
-    print(f"work to first: plain {plain.sum():.3e} learned {learned.sum():.3e} "
-          f"(ratio {learned.sum() / plain.sum():.3f}); per instance ratios "
-          f"{np.round((learned + 1) / (plain + 1), 3).tolist()}")
-    assert learned.sum() < plain.sum()
-    assert np.exp(np.mean(np.log((learned + 1) / (plain + 1)))) < 1.0
+    work, rank = w.ratios()
+    print(f"learned / plain, geometric means over {len(held)} instances: work before the first "
+          f"solution-bearing subtree {work:.3f}, its queue position {rank:.3f}")
+    assert work < 0.8
+    assert rank < 0.2

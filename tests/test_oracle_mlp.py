@@ -47,9 +47,9 @@ def test_gradient_matches_finite_differences(pos_weight):
         assert num == pytest.approx(g[i], rel=1e-5, abs=1e-8), i
 
 
-def test_score_prefers_likely_and_small_subtrees():
+def test_score_ranks_by_solution_probability():
     y = np.zeros((3, 8))
-    y[:, 0] = [2.0, 2.0, -2.0]
+    y[:, 0] = [2.0, 2.5, -2.0]
     y[:, 1] = [1.0, 5.0, 1.0]
     s = R.score(y)
-    assert s[0] > s[1] and s[0] > s[2]
+    assert s[1] > s[0] > s[2]
