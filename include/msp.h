@@ -101,6 +101,9 @@ typedef struct {
                            /*       exhausts a tree, whose paths have at most 127 levels) */
     int first_split_target; /* [16384] split target of MSP_FIRST when split_target = 0: */
                            /*       small subtrees let a good queue order pay off        */
+    int bkz_beta;          /* [0] >= 2: BKZ-beta of the kernel basis after LLL (Sec. 2   */
+                           /*     names LLL or BKZ for step 1); 0: LLL only              */
+    int bkz_max_tours;     /* [16] BKZ tours at most (a tour without insertion ends it) */
 } msp_opts;
 
 /* Per-instance results of an enumeration. */
@@ -128,6 +131,9 @@ typedef struct {
     int32_t lds_budget;    /* MSP_LDS: budget of the iteration that solved (MSP_FIRST) or */
                            /* finished (MSP_ALL) this instance; -1 otherwise            */
     double ms;             /* wall time of the enumeration call (whole batch)          */
+    int64_t bkz_tours;     /* BKZ tours run (0 without BKZ)                            */
+    int64_t bkz_inserts;   /* block shortest vectors inserted                         */
+    int64_t bkz_nodes;     /* enumeration nodes of the block searches                 */
 } msp_stats;
 
 typedef struct msp_ctx msp_ctx;

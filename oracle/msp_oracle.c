@@ -20,6 +20,10 @@
  *                           norm test (first pruning condition), the Hoelder
  *                           test of Theorem 2 with the one-direction cut,
  *                           exact leaf test of Theorem 1  [Sec. 2, Alg. 1]
+ *   6. BKZ                  blockwise Korkine-Zolotarev reduction of the
+ *                           kernel basis (the alternative to LLL that Sec. 2
+ *                           names for step 1): block-wise shortest vectors
+ *                           by enumeration, inserted, then LLL   [Sec. 2]
  *
  * Readings where the paper is silent or ambiguous (all fixed here and used
  * identically by the GPU path, which implements them independently):
@@ -522,6 +526,176 @@ int oracle_enumerate(int dd, int dim, const double *mu, const double *B, const d
     *out = e.s;
     free(e.u); free(e.vbuf); free(e.xbuf); free(w0);
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 6. BKZ-beta on the kernel basis (Sec. 2 names "LLL or blockwise           */
+/* Korkine-Zolotarev reduction" for step 1; the paper gives no parameters).  */
+/* Readings (R13):                                                           */
+/*   - BKZ runs on the kept kernel basis after LLL and extraction (the same */
+/*     lattice the enumeration walks; the rows scaled by N play no part).   */
+/*   - A tour visits k = 0 .. dd-2 with the block [k, h), h = min(k+beta,   */
+/*     dd).  The block's shortest nonzero projected vector is found by     */
+/*     Schnorr-Euchner enumeration (no Hoelder test: it is a general       */
+/*     shortest vector search) with the bound delta * B_k, strict, shrunk  */
+/*     to every improvement; ties keep the first found.  The tree has the  */
+/*     same order and arithmetic as R2/R6/R9: zig-zag around the rounded   */
+/*     centre, u >= 0 on all-zero top levels.                              */
+/*   - An improvement u (primitive) is inserted by unimodular steps on the */
+/*     rows k .. h-1: from the last row down, each pair (c_{i-1}, c_i) with */
+/*     coefficients (a, b), g = gcd(a, b) = s a + t b, becomes            */
+/*     ((a/g) c_{i-1} + (b/g) c_i, -t c_{i-1} + s c_i), moving the         */
+/*     coefficient g one row up; then row k equals the inserted vector and */
+/*     the whole basis is LLL-reduced again (delta, eta = 0.51).           */
+/*   - Tours repeat until one inserts nothing, or max_tours.               */
+/*   - GSO per block from the exact Gram matrix, divided form of Eq. (4).  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int dd, h, k;
+    const double *mu, *B;
+    double A;            /* current bound (strict) */
+    int32_t *u, *best;
+    int found;
+    int64_t nodes;
+} svp_state;
+
+static void svp_level(svp_state *e, int t, double rho_p)
+{
+    const int dd = e->dd, h = e->h;
+    int zero_prefix = 1;
+    for (int i = t + 1; i < h; ++i) if (e->u[i] != 0) { zero_prefix = 0; break; }
+    double acc = 0.0;
+    for (int i = h - 1; i > t; --i) acc = fma((double)e->u[i], e->mu[(size_t)i * dd + t], acc);
+    const double y = acc, cstar = -y;
+    long u1 = (long)rint(cstar);
+    const int s = (cstar >= (double)u1) ? 1 : -1;
+    long zi = 1, u = u1;
+    if (zero_prefix) u = u1 = 0;
+    for (;;) {
+        const double x = (double)u + y;
+        const double rho = fma(x * x, e->B[t], rho_p);
+        e->nodes++;
+        if (!(rho < e->A)) return;
+        e->u[t] = (int32_t)u;
+        if (t == e->k) {
+            if (!(zero_prefix && u == 0)) {      /* nonzero vector: an improvement */
+                e->A = rho;
+                memcpy(e->best + e->k, e->u + e->k, sizeof(int32_t) * (size_t)(h - e->k));
+                e->found = 1;
+            }
+        } else {
+            svp_level(e, t - 1, rho);
+        }
+        e->u[t] = 0;
+        if (zero_prefix) ++u;
+        else { ++zi; u = (zi % 2 == 0) ? u1 + (long)s * (zi / 2) : u1 - (long)s * ((zi - 1) / 2); }
+    }
+}
+
+static int64_t egcd64(int64_t a, int64_t b, int64_t *sa, int64_t *tb)
+{
+    int64_t r0 = a < 0 ? -a : a, r1 = b < 0 ? -b : b, s0 = 1, s1 = 0, t0 = 0, t1 = 1;
+    while (r1 != 0) {
+        const int64_t q = r0 / r1, r2 = r0 - q * r1, s2 = s0 - q * s1, t2 = t0 - q * t1;
+        r0 = r1; r1 = r2; s0 = s1; s1 = s2; t0 = t1; t1 = t2;
+    }
+    *sa = a < 0 ? -s0 : s0;
+    *tb = b < 0 ? -t0 : t0;
+    return r0;
+}
+
+/* b: dd x dim int64, BKZ-reduced in place.  Returns OR_OK, OR_EOVERFLOW,
+ * OR_ECAP or OR_ENOMEM.  stats: tours run, insertions, enumeration nodes. */
+int oracle_bkz(int dd, int dim, int64_t *b, int beta, double delta, int max_tours, int64_t lll_max_iter,
+               int64_t *tours_out, int64_t *inserts_out, int64_t *nodes_out)
+{
+    if (dd < 1 || beta < 2) return OR_EINVAL;
+    int st = OR_OK;
+    int64_t tours = 0, inserts = 0, nodes = 0;
+    double *mu = (double *)calloc((size_t)dd * dd, sizeof(double));
+    double *r = (double *)calloc((size_t)dd * dd, sizeof(double));
+    double *B = (double *)calloc((size_t)dd, sizeof(double));
+    int64_t *G = (int64_t *)calloc((size_t)dd * dd, sizeof(int64_t));
+    int64_t *rows = (int64_t *)calloc((size_t)dd * dim, sizeof(int64_t));
+    int32_t *u = (int32_t *)calloc((size_t)dd, sizeof(int32_t));
+    int32_t *best = (int32_t *)calloc((size_t)dd, sizeof(int32_t));
+    int64_t *a = (int64_t *)calloc((size_t)dd, sizeof(int64_t));
+    if (!mu || !r || !B || !G || !rows || !u || !best || !a) { st = OR_ENOMEM; goto done; }
+    for (int tour = 0; tour < max_tours; ++tour) {
+        int inserted = 0;
+        ++tours;
+        for (int k = 0; k + 1 < dd; ++k) {
+            const int h = (k + beta < dd) ? k + beta : dd;
+            /* GSO of the current basis (exact Gram, Eq. (4) divided form) */
+            for (int i = 0; i < dd; ++i)
+                for (int j = 0; j <= i; ++j) {
+                    int64_t g;
+                    if ((st = dot_exact(b + (size_t)i * dim, b + (size_t)j * dim, dim, &g))) goto done;
+                    G[(size_t)i * dd + j] = g;
+                    G[(size_t)j * dd + i] = g;
+                }
+            for (int i = 0; i < dd; ++i) {
+                for (int j = 0; j < i; ++j) {
+                    double acc = (double)G[(size_t)i * dd + j];
+                    for (int q = 0; q < j; ++q) acc = fma(-mu[(size_t)j * dd + q], r[(size_t)i * dd + q], acc);
+                    r[(size_t)i * dd + j] = acc;
+                    mu[(size_t)i * dd + j] = acc / B[j];
+                }
+                double acc = (double)G[(size_t)i * dd + i];
+                for (int q = 0; q < i; ++q) acc = fma(-mu[(size_t)i * dd + q], r[(size_t)i * dd + q], acc);
+                B[i] = acc;
+            }
+            /* shortest nonzero vector of the projected block */
+            svp_state e;
+            memset(&e, 0, sizeof e);
+            e.dd = dd; e.h = h; e.k = k; e.mu = mu; e.B = B;
+            e.A = delta * B[k];
+            e.u = u; e.best = best;
+            memset(u, 0, sizeof(int32_t) * (size_t)dd);
+            svp_level(&e, h - 1, 0.0);
+            nodes += e.nodes;
+            if (!e.found) continue;
+            /* insertion by unimodular row steps (R13) */
+            memcpy(rows, b + (size_t)k * dim, sizeof(int64_t) * (size_t)(h - k) * dim);
+            for (int i = k; i < h; ++i) a[i - k] = best[i];
+            for (int i = h - k - 1; i > 0; --i) {
+                if (a[i] == 0) continue;
+                int64_t *c0 = rows + (size_t)(i - 1) * dim, *c1 = rows + (size_t)i * dim;
+                if (a[i - 1] == 0) {
+                    for (int c = 0; c < dim; ++c) { int64_t t = c0[c]; c0[c] = c1[c]; c1[c] = t; }
+                    a[i - 1] = a[i];
+                    a[i] = 0;
+                    continue;
+                }
+                int64_t sa, tb;
+                const int64_t g = egcd64(a[i - 1], a[i], &sa, &tb);
+                const int64_t p = a[i - 1] / g, q = a[i] / g;
+                for (int c = 0; c < dim; ++c) {
+                    const i128 v0 = (i128)p * c0[c] + (i128)q * c1[c];
+                    const i128 v1 = -(i128)tb * c0[c] + (i128)sa * c1[c];
+                    if (v0 >= OR_ENTRY_LIMIT || v0 <= -OR_ENTRY_LIMIT || v1 >= OR_ENTRY_LIMIT ||
+                        v1 <= -OR_ENTRY_LIMIT) { st = OR_EOVERFLOW; goto done; }
+                    c0[c] = (int64_t)v0;
+                    c1[c] = (int64_t)v1;
+                }
+                a[i - 1] = g;
+                a[i] = 0;
+            }
+            if (a[0] != 1 && a[0] != -1) continue;   /* not primitive: cannot be a basis vector */
+            if (a[0] == -1) for (int c = 0; c < dim; ++c) rows[c] = -rows[c];
+            memcpy(b + (size_t)k * dim, rows, sizeof(int64_t) * (size_t)(h - k) * dim);
+            if ((st = oracle_lll(dd, dim, b, delta, 0.51, lll_max_iter, NULL, NULL))) goto done;
+            ++inserts;
+            inserted = 1;
+        }
+        if (!inserted) break;
+    }
+done:
+    if (tours_out) *tours_out = tours;
+    if (inserts_out) *inserts_out = inserts;
+    if (nodes_out) *nodes_out = nodes;
+    free(mu); free(r); free(B); free(G); free(rows); free(u); free(best); free(a);
+    return st;
 }
 
 /* Version tag so tests can check they loaded this file's build. */

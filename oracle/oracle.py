@@ -55,6 +55,7 @@ def lib():
         L.oracle_lll.argtypes = [C.c_int, C.c_int, P, C.c_double, C.c_double, C.c_int64, P, P]
         L.oracle_extract.argtypes = [C.c_int, C.c_int, P, P, P]
         L.oracle_gso.argtypes = [C.c_int, C.c_int, P, P, P, P]
+        L.oracle_bkz.argtypes = [C.c_int, C.c_int, P, C.c_int, C.c_double, C.c_int, C.c_int64, P, P, P]
         L.oracle_enumerate.argtypes = [C.c_int, C.c_int, P, P, P, P, C.c_int, C.c_int, P, P,
                                        C.POINTER(_EnumOpts), P, P, C.c_int64, P, P, C.c_int64,
                                        C.POINTER(_EnumStats)]
@@ -127,6 +128,28 @@ def gso(kern: np.ndarray) -> GSO:
     bhat = np.zeros((dd, dim), np.float64)
     _check(lib().oracle_gso(dd, dim, _p(kb), _p(mu), _p(B), _p(bhat)), "gso")
     return GSO(mu, B, bhat)
+
+
+@dataclass
+class BKZResult:
+    kern: np.ndarray      # (dd, dim) int32, BKZ-reduced kernel basis
+    tours: int
+    inserts: int
+    nodes: int            # enumeration nodes of the block searches
+
+
+def bkz(kern: np.ndarray, beta: int, delta: float = 0.99, max_tours: int = 16,
+        lll_max_iter: int = 50_000_000) -> BKZResult:
+    """BKZ-beta of the kernel basis (Sec. 2; readings in the C file, R13)."""
+    b = np.ascontiguousarray(kern, dtype=np.int64).copy()
+    dd, dim = b.shape
+    t = np.zeros(1, np.int64)
+    ins = np.zeros(1, np.int64)
+    nd = np.zeros(1, np.int64)
+    _check(lib().oracle_bkz(dd, dim, _p(b), beta, delta, max_tours, lll_max_iter, _p(t), _p(ins), _p(nd)), "bkz")
+    if np.abs(b).max(initial=0) >= 2 ** 31:
+        raise OracleError("bkz: entry outside int32")
+    return BKZResult(b.astype(np.int32), int(t[0]), int(ins[0]), int(nd[0]))
 
 
 @dataclass

@@ -17,7 +17,9 @@
 namespace msp {
 __global__ void build_lattice_kernel(Pools P, int64_t N);
 __global__ void lll_kernel(Pools P, double delta, double eta, int64_t max_iter, unsigned long long max_ns);
-__global__ void extract_gso_kernel(Pools P);
+__global__ void extract_gso_kernel(Pools P, int gso_only);
+__global__ void bkz_kernel(Pools P, BkzScratch S, int beta, double delta, int max_tours, int64_t lll_max_iter,
+                           unsigned long long max_ns);
 __global__ void prep_fixed_kernel(Pools P, int use_eps, int dimPad);
 cudaError_t launch_split(const Pools& P, const EnumCfg& cfg, int lanes, int max_depth, int64_t target,
                          int64_t* fcnt, cudaStream_t st);
@@ -78,7 +80,7 @@ struct msp_ctx {
     // device buffers
     Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, bq, nbq, fu, fdisc, fxsum, frho, fw, fcnt, qbase, sols, ctrl, soff,
         fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_seq, feat, prof, yout, skeys, svals, skeys2,
-        svals2, perm, theta, mlpwork, inst0, skip;
+        svals2, perm, theta, mlpwork, inst0, skip, bkzs;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cst = nullptr;          // private stream the step is captured on
@@ -286,6 +288,8 @@ void msp_default_opts(msp_opts* o) {
     o->lds_budget = -1;
     o->lds_max = 127;
     o->first_split_target = 16384;
+    o->bkz_beta = 0;
+    o->bkz_max_tours = 16;
 }
 
 const char* msp_status_string(int s) {
@@ -320,7 +324,8 @@ msp_status msp_create(msp_ctx** out, const msp_opts* opts, void* stream) {
         o.hoelder < 0 || o.hoelder > 2 || (o.lanes != 4 && o.lanes != 8 && o.lanes != 16 && o.lanes != 32) ||
         o.split_depth < 0 || o.warps_per_block < 1 || o.warps_per_block > 8 || o.sol_capacity < 1 ||
         o.lll_max_iter < 1 || !(o.max_seconds > 0.0) || o.donation_capacity < 0 || o.lds_budget < -1 ||
-        o.lds_budget > 127 || o.lds_max < 0 || o.lds_max > 127 || o.first_split_target < 0) {
+        o.lds_budget > 127 || o.lds_max < 0 || o.lds_max > 127 || o.first_split_target < 0 ||
+        o.bkz_beta < 0 || o.bkz_beta == 1 || o.bkz_beta > 128 || o.bkz_max_tours < 1) {
         delete c;
         return MSP_EINVAL;
     }
@@ -350,7 +355,7 @@ void msp_destroy(msp_ctx* c) {
                   &c->bhat, &c->bq, &c->nbq, &c->fdisc, &c->fxsum, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
                   &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols, &c->don,
                   &c->don_seq, &c->feat, &c->prof, &c->yout, &c->skeys, &c->svals, &c->skeys2, &c->svals2,
-                  &c->perm, &c->theta, &c->mlpwork, &c->inst0, &c->skip};
+                  &c->perm, &c->theta, &c->mlpwork, &c->inst0, &c->skip, &c->bkzs};
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->cst) cudaStreamDestroy(c->cst);
@@ -466,9 +471,21 @@ msp_status msp_reduce(msp_ctx* c) {
     ++c->launches;
     msp_status s = check_launch(c, "lll_kernel");
     if (s != MSP_OK) return s;
-    extract_gso_kernel<<<c->count, 32, 0, c->st>>>(c->P);
+    extract_gso_kernel<<<c->count, 32, 0, c->st>>>(c->P, 0);
     ++c->launches;
     if ((s = check_launch(c, "extract_gso_kernel")) != MSP_OK) return s;
+    if (c->o.bkz_beta >= 2) {   // BKZ of the kernel basis, then its tables again
+        BkzScratch S{nullptr, BkzScratch::bytes(c->Kmax, c->dimMax), c->Kmax, c->dimMax};
+        if ((s = ensure(c, c->bkzs, (size_t)S.stride * c->count, "bkz scratch")) != MSP_OK) return s;
+        S.base = ptr<char>(c->bkzs);
+        bkz_kernel<<<c->count, 32, 0, c->st>>>(c->P, S, c->o.bkz_beta, c->o.delta, c->o.bkz_max_tours,
+                                               c->o.lll_max_iter, (unsigned long long)(c->o.max_seconds * 1e9));
+        ++c->launches;
+        if ((s = check_launch(c, "bkz_kernel")) != MSP_OK) return s;
+        extract_gso_kernel<<<c->count, 32, 0, c->st>>>(c->P, 1);
+        ++c->launches;
+        if ((s = check_launch(c, "extract_gso_kernel")) != MSP_OK) return s;
+    }
     prep_fixed_kernel<<<c->count, 32, 0, c->st>>>(c->P, c->o.use_eps, c->dimPad);
     ++c->launches;
     if ((s = check_launch(c, "prep_fixed_kernel")) != MSP_OK) return s;
@@ -716,6 +733,9 @@ msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {
         S.kernel_rank = h[i].dd;
         S.lll_iterations = h[i].lll_iters;
         S.lll_swaps = h[i].lll_swaps;
+        S.bkz_tours = h[i].bkz_tours;
+        S.bkz_inserts = h[i].bkz_inserts;
+        S.bkz_nodes = h[i].bkz_nodes;
         S.split_nodes = (int64_t)cn[i].split_nodes;
         S.split_passed = (int64_t)cn[i].split_passed;
         S.center_fma = (int64_t)cn[i].center_fma;
@@ -735,6 +755,9 @@ msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {
         tot.prefixes += S.prefixes;
         tot.lll_iterations += S.lll_iterations;
         tot.lll_swaps += S.lll_swaps;
+        tot.bkz_tours += S.bkz_tours;
+        tot.bkz_inserts += S.bkz_inserts;
+        tot.bkz_nodes += S.bkz_nodes;
         tot.split_nodes += S.split_nodes;
         tot.split_passed += S.split_passed;
         tot.center_fma += S.center_fma;

@@ -37,6 +37,7 @@ struct InstDesc {
     int64_t offB;            // K f64       ||bhat_t||^2
     int64_t offBhat;         // K*dim f64   bhat[t][c]
     int64_t lll_iters, lll_swaps;
+    int64_t bkz_tours, bkz_inserts, bkz_nodes;   // BKZ of the kernel basis (0 without BKZ)
     // fixed-point filter of the Hoelder test (set by prep_fixed_kernel)
     int32_t sx, sb;          // scales: Xq = trunc(x 2^sx), Bq = round(bhat 2^sb)
     int64_t offBq;           // K*dimPad int32   Bq[t][c]
@@ -119,6 +120,20 @@ struct Ctrl {
 };
 
 // Enumeration options passed to the split and enumeration kernels.
+// Per-instance global scratch of the BKZ kernel: two K x D int64 blocks
+// (basis, block copy), three K x K blocks (Gram, mu, r), six K-vectors of
+// 8 bytes and five of 4 bytes; the stride is rounded to 256 bytes.
+struct BkzScratch {
+    char* base;
+    int64_t stride;   // bytes per instance
+    int Kmax, dimMax;
+    __host__ __device__ static int64_t bytes(int Kmax, int dimMax) {
+        const int64_t K = Kmax, D = dimMax;
+        const int64_t raw = 8 * (2 * K * D + 3 * K * K + 6 * K) + 4 * 5 * K;
+        return (raw + 255) / 256 * 256;
+    }
+};
+
 struct EnumCfg {
     int hoelder;     // 0: Hoelder test with the one-direction cut, 1: skip value only, 2: off
     int sym;         // 1: one of v, -v;  0: both signs

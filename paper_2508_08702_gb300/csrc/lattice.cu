@@ -95,24 +95,18 @@ __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ 
     __syncwarp();
 }
 
-// Step a2: delta-LLL, one warp per instance (blockDim.x == 32).
-__global__ void __launch_bounds__(32) lll_kernel(Pools P, double delta, double eta, int64_t max_iter,
-                                                 unsigned long long max_ns) {
-    InstDesc& I = P.inst[blockIdx.x];
-    const int lane = threadIdx.x;
-    if (I.status != ST_OK) return;
-    const unsigned long long t_start = global_time_ns();
-    const int K = I.K, L = I.L;
-    int64_t* b = P.basis + I.offBasis;
-    int64_t* G = P.gram + I.offGram;
-    double* mu = P.mu + I.offMu;
-    double* r = mu + (int64_t)K * K;
-    double* invB = r + (int64_t)K * K;
-    double* B = P.Bl + I.offBl;
+// delta-LLL of K vectors of length L (int64, vector-major, in place) by one
+// warp: exact Gram matrix G (K x K), FP64 Gram-Schmidt rows recomputed from
+// it (mu, r: K x K; invB, B: K), lazy size reduction, Lovasz swaps.
+// Returns a status; iterations and swaps are added to the counters.
+__device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, double* __restrict__ mu,
+                            double* __restrict__ r, double* __restrict__ invB, double* __restrict__ B, int K, int L,
+                            double delta, double eta, int64_t max_iter, unsigned long long deadline_ns,
+                            int64_t& iters, int64_t& swaps) {
+    const int lane = threadIdx.x & 31;
     auto mu_at = [&](int j, int i) { return mu[(int64_t)j * K + i]; };
     int32_t st = ST_OK;
-    int64_t iters = 0, swaps = 0;
-
+    int64_t it = 0;
     // exact Gram matrix
     {
         bool ovf = false;
@@ -131,10 +125,10 @@ __global__ void __launch_bounds__(32) lll_kernel(Pools P, double delta, double e
 
     int k = 1;
     while (st == ST_OK && k < K) {
-        if (++iters > max_iter) { st = ST_ECAP; break; }
-        if ((iters & 255) == 0) {   // device-clock safety cap (uniform across the warp)
+        if (++it > max_iter) { st = ST_ECAP; break; }
+        if ((it & 255) == 0) {   // device-clock safety cap (uniform across the warp)
             const unsigned long long now = __shfl_sync(kFull, global_time_ns(), 0);
-            if (now - t_start > max_ns) { st = ST_ECAP; break; }
+            if (now > deadline_ns) { st = ST_ECAP; break; }
         }
         // lazy size reduction of b_k
         for (int pass = 0;; ++pass) {
@@ -205,7 +199,22 @@ __global__ void __launch_bounds__(32) lll_kernel(Pools P, double delta, double e
             ++k;
         }
     }
-    if (lane == 0) {
+    iters += it;
+    return st;
+}
+
+// Step a2: delta-LLL of the generator lattice, one warp per instance.
+__global__ void __launch_bounds__(32) lll_kernel(Pools P, double delta, double eta, int64_t max_iter,
+                                                 unsigned long long max_ns) {
+    InstDesc& I = P.inst[blockIdx.x];
+    if (I.status != ST_OK) return;
+    const int K = I.K, L = I.L;
+    double* mu = P.mu + I.offMu;
+    int64_t iters = 0, swaps = 0;
+    const int32_t st = lll_warp(P.basis + I.offBasis, P.gram + I.offGram, mu, mu + (int64_t)K * K,
+                                mu + (int64_t)2 * K * K, P.Bl + I.offBl, K, L, delta, eta, max_iter,
+                                __shfl_sync(kFull, global_time_ns(), 0) + max_ns, iters, swaps);
+    if (threadIdx.x == 0) {
         I.lll_iters = iters;
         I.lll_swaps = swaps;
         if (st != ST_OK) set_status(I, st);
@@ -235,12 +244,17 @@ __device__ int rank_mod_p(int64_t* M, int rows, int cols) {
     return rank;
 }
 
-// Step a3: extraction and Gram-Schmidt of the kernel basis, one warp per instance.
-__global__ void __launch_bounds__(32) extract_gso_kernel(Pools P) {
+// Step a3: extraction and Gram-Schmidt of the kernel basis, one warp per
+// instance.  gso_only: the kernel basis is already in place (after BKZ);
+// only the Gram-Schmidt tables are recomputed.
+__global__ void __launch_bounds__(32) extract_gso_kernel(Pools P, int gso_only) {
     InstDesc& I = P.inst[blockIdx.x];
     const int lane = threadIdx.x;
     if (I.status != ST_OK) return;
     const int m = I.m, K = I.K, L = I.L, dim = I.n + 1;
+    int32_t* kb = P.kb + I.offKb;
+    int dd = I.dd;
+    if (!gso_only) {
     const int64_t* b = P.basis + I.offBasis;
     // kept flags (vectors whose first m entries vanish), in reduced order
     unsigned kept_mask[4];
@@ -254,7 +268,7 @@ __global__ void __launch_bounds__(32) extract_gso_kernel(Pools P) {
         }
         kept_mask[q] = __ballot_sync(kFull, z);
     }
-    int dd = 0;
+    dd = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) dd += __popc(kept_mask[q]);
     const int mp = K - dd;   // vectors with a nonzero top part
@@ -276,7 +290,6 @@ __global__ void __launch_bounds__(32) extract_gso_kernel(Pools P) {
     }
     st = __shfl_sync(kFull, st, 0);
     // copy the kept vectors without their top rows
-    int32_t* kb = P.kb + I.offKb;
     bool ovf = false;
     for (int k = 0; k < K && st == ST_OK; ++k) {
         if (!((kept_mask[k >> 5] >> (k & 31)) & 1u)) continue;
@@ -295,6 +308,7 @@ __global__ void __launch_bounds__(32) extract_gso_kernel(Pools P) {
         if (lane == 0) set_status(I, st);
         return;
     }
+    }   // !gso_only
     // exact Gram matrix of the kernel basis (entries < 2^20 -> no overflow)
     int64_t* G = P.gram + I.offGram;
     for (int e = lane; e < dd * dd; e += 32) {
@@ -335,6 +349,212 @@ __global__ void __launch_bounds__(32) extract_gso_kernel(Pools P) {
         __syncwarp();
     }
     if (lane == 0) { I.dd = dd; I.dim = dim; }
+}
+
+// ---------------------------------------------------------------------------
+// BKZ-beta of the kernel basis (Sec. 2: "LLL or blockwise Korkine-Zolotarev
+// reduction"), one warp per instance, after extraction.  A tour visits the
+// blocks [k, h), h = min(k + beta, dd), k = 0 .. dd-2: the Gram-Schmidt data
+// of the whole basis is rebuilt (exact Gram matrix, Eq. (4) divided form),
+// the block's shortest nonzero projected vector is searched by
+// Schnorr-Euchner enumeration (lane 0; bound delta B_k, strict, shrunk to
+// each improvement; zig-zag order and u >= 0 on all-zero top levels as in
+// the main enumeration; no Hoelder test), and an improvement u is inserted
+// by unimodular row steps -- from the last row of the block upwards, rows
+// (c, c') with coefficients (a, b), g = gcd(a, b) = s a + t b, become
+// ((a/g) c + (b/g) c', -t c + s c') -- after which the whole basis is
+// LLL-reduced again.  Tours repeat until one inserts nothing.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t egcd64(int64_t a, int64_t b, int64_t& sa, int64_t& tb) {
+    int64_t r0 = a < 0 ? -a : a, r1 = b < 0 ? -b : b, s0 = 1, s1 = 0, t0 = 0, t1 = 1;
+    while (r1 != 0) {
+        const int64_t q = r0 / r1, r2 = r0 - q * r1, s2 = s0 - q * s1, t2 = t0 - q * t1;
+        r0 = r1; r1 = r2; s0 = s1; s1 = s2; t0 = t1; t1 = t2;
+    }
+    sa = a < 0 ? -s0 : s0;
+    tb = b < 0 ? -t0 : t0;
+    return r0;
+}
+
+__global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta, double delta, int max_tours,
+                                                 int64_t lll_max_iter, unsigned long long max_ns) {
+    InstDesc& I = P.inst[blockIdx.x];
+    const int lane = threadIdx.x;
+    if (I.status != ST_OK) return;
+    const int dd = I.dd, dim = I.dim, K = S.Kmax, D = S.dimMax;
+    char* sp = S.base + (int64_t)blockIdx.x * S.stride;
+    int64_t* b = reinterpret_cast<int64_t*>(sp);                 // dd x dim
+    int64_t* rows = b + (int64_t)K * D;                           // block copy
+    int64_t* G = rows + (int64_t)K * D;                           // dd x dd
+    double* mu = reinterpret_cast<double*>(G + (int64_t)K * K);   // dd x dd
+    double* r = mu + (int64_t)K * K;
+    double* invB = r + (int64_t)K * K;
+    double* B = invB + K;
+    double* yv = B + K;                                           // SVP: centre per level
+    double* rhoP = yv + K;                                        // SVP: parent norm per level
+    int64_t* a = reinterpret_cast<int64_t*>(rhoP + K);
+    double* Bsvp = reinterpret_cast<double*>(a + K);              // unused slot kept for alignment
+    int32_t* u = reinterpret_cast<int32_t*>(Bsvp + K);
+    int32_t* best = u + K;
+    int32_t* u1v = best + K;
+    int32_t* ziv = u1v + K;
+    int32_t* flg = ziv + K;                                       // bit 0 zero prefix, bit 1 negative side
+    int32_t* kb = P.kb + I.offKb;
+    const unsigned long long deadline = __shfl_sync(kFull, global_time_ns(), 0) + max_ns;   // uniform
+    auto mu_at = [&](int j, int i) { return mu[(int64_t)j * dd + i]; };
+
+    for (int e = lane; e < dd * dim; e += 32) b[e] = kb[e];
+    __syncwarp();
+    int32_t st = ST_OK;
+    int64_t tours = 0, inserts = 0, nodes = 0, iters = 0, swaps = 0;
+    for (int tour = 0; tour < max_tours && st == ST_OK; ++tour) {
+        ++tours;
+        bool inserted = false;
+        for (int k = 0; k + 1 < dd && st == ST_OK; ++k) {
+            const int h = min(k + beta, dd);
+            // Gram-Schmidt data of the current basis (exact Gram, divided mu)
+            bool ovf = false;
+            for (int e = lane; e < dd * dd; e += 32) {
+                const int i = e / dd, j = e % dd;
+                if (j <= i) {
+                    const int64_t g = dot_exact(b + (int64_t)i * dim, b + (int64_t)j * dim, dim, ovf);
+                    G[(int64_t)i * dd + j] = g;
+                    G[(int64_t)j * dd + i] = g;
+                }
+            }
+            if (__any_sync(kFull, ovf)) { st = ST_EOVERFLOW; break; }
+            __syncwarp();
+            for (int i = 0; i < dd; ++i)
+                gso_row_warp(i, G + (int64_t)i * dd, mu_at, B, r + (int64_t)i * dd, mu + (int64_t)i * dd, &B[i],
+                             lane);
+            bool badB = false;   // a level with B_t <= 0 would never end its zig-zag
+            for (int i = lane; i < dd; i += 32) badB |= !(B[i] > 0.0 && B[i] < 1e300);
+            if (__any_sync(kFull, badB)) { st = ST_EOVERFLOW; break; }
+            // shortest nonzero vector of the projected block (lane 0)
+            int found = 0;
+            if (lane == 0) {
+                double A = __dmul_rn(delta, B[k]);
+                for (int i = 0; i < dd; ++i) u[i] = 0;
+                int t = h - 1;
+                rhoP[t] = 0.0;
+                bool enter = true;
+                long long nloc = 0;
+                for (;;) {
+                    int cur;
+                    if (enter) {
+                        bool zp = true;
+                        for (int i = t + 1; i < h; ++i) if (u[i] != 0) { zp = false; break; }
+                        double acc = 0.0;
+                        for (int i = h - 1; i > t; --i) acc = __fma_rn((double)u[i], mu[(int64_t)i * dd + t], acc);
+                        yv[t] = acc;
+                        const double cstar = -acc;
+                        const double r1 = rint(cstar);
+                        if (fabs(r1) > 1e9) { st = ST_EOVERFLOW; break; }
+                        int uu = (int)r1;
+                        const int sgn = (cstar >= r1) ? 1 : -1;
+                        if (zp) uu = 0;
+                        u1v[t] = uu;
+                        ziv[t] = 1;
+                        flg[t] = (zp ? 1 : 0) | (sgn < 0 ? 2 : 0);
+                        cur = uu;
+                        enter = false;
+                    } else {
+                        // next value of level t
+                        u[t] = 0;
+                        if (flg[t] & 1) {
+                            cur = u1v[t] + ziv[t];   // 0, 1, 2, ... (zi counts the steps)
+                            ++ziv[t];
+                        } else {
+                            const int zi = ++ziv[t];
+                            const int sgn = (flg[t] & 2) ? -1 : 1;
+                            cur = (zi % 2 == 0) ? u1v[t] + sgn * (zi / 2) : u1v[t] - sgn * ((zi - 1) / 2);
+                        }
+                    }
+                    const double x = __dadd_rn((double)cur, yv[t]);
+                    const double rho = __fma_rn(__dmul_rn(x, x), B[t], rhoP[t]);
+                    ++nloc;
+                    if ((nloc & 4095) == 0 && global_time_ns() > deadline) { st = ST_ECAP; break; }
+                    if (!(rho < A)) {   // level exhausted: back to the parent
+                        u[t] = 0;
+                        if (t == h - 1) break;
+                        ++t;
+                        continue;
+                    }
+                    u[t] = cur;
+                    if (t == k) {
+                        if (!((flg[t] & 1) && cur == 0)) {
+                            A = rho;
+                            for (int i = k; i < h; ++i) best[i] = u[i];
+                            found = 1;
+                        }
+                    } else {
+                        rhoP[t - 1] = rho;
+                        --t;
+                        enter = true;
+                    }
+                }
+                nodes += nloc;
+            }
+            st = __shfl_sync(kFull, st, 0);
+            found = __shfl_sync(kFull, found, 0);
+            if (st != ST_OK || !found) continue;
+            // insertion by unimodular row steps
+            const int nb = h - k;
+            for (int e = lane; e < nb * dim; e += 32) rows[e] = b[(int64_t)k * dim + e];
+            if (lane == 0) for (int i = 0; i < nb; ++i) a[i] = best[k + i];
+            __syncwarp();
+            bool bad = false;
+            for (int i = nb - 1; i > 0; --i) {
+                const int64_t ai = a[i], am = a[i - 1];
+                if (ai == 0) continue;
+                int64_t* c0 = rows + (int64_t)(i - 1) * dim;
+                int64_t* c1 = rows + (int64_t)i * dim;
+                if (am == 0) {
+                    for (int c = lane; c < dim; c += 32) { const int64_t t0 = c0[c]; c0[c] = c1[c]; c1[c] = t0; }
+                    __syncwarp();
+                    if (lane == 0) { a[i - 1] = ai; a[i] = 0; }
+                    __syncwarp();
+                    continue;
+                }
+                int64_t sa, tb;
+                const int64_t g = egcd64(am, ai, sa, tb);
+                const int64_t p = am / g, q = ai / g;
+                for (int c = lane; c < dim; c += 32) {
+                    const __int128 v0 = (__int128)p * c0[c] + (__int128)q * c1[c];
+                    const __int128 v1 = -(__int128)tb * c0[c] + (__int128)sa * c1[c];
+                    if (v0 >= kEntryLimit || v0 <= -kEntryLimit || v1 >= kEntryLimit || v1 <= -kEntryLimit) bad = true;
+                    c0[c] = (int64_t)v0;
+                    c1[c] = (int64_t)v1;
+                }
+                __syncwarp();
+                if (lane == 0) { a[i - 1] = g; a[i] = 0; }
+                __syncwarp();
+            }
+            if (__any_sync(kFull, bad)) { st = ST_EOVERFLOW; break; }
+            const int64_t a0 = a[0];
+            if (a0 != 1 && a0 != -1) continue;   // not primitive (cannot happen for a shortest vector)
+            for (int e = lane; e < nb * dim; e += 32)
+                b[(int64_t)k * dim + e] = (a0 == -1 && e < dim) ? -rows[e] : rows[e];
+            __syncwarp();
+            st = lll_warp(b, G, mu, r, invB, B, dd, dim, delta, 0.51, lll_max_iter, deadline, iters, swaps);
+            ++inserts;
+            inserted = true;
+        }
+        if (!inserted) break;
+    }
+    // back to the int32 kernel basis (the enumeration's entries stay below 2^20)
+    bool ovf = false;
+    for (int e = lane; e < dd * dim && st == ST_OK; e += 32) {
+        if (b[e] >= (1 << 20) || b[e] <= -(1 << 20)) ovf = true;
+        else kb[e] = (int32_t)b[e];
+    }
+    if (__any_sync(kFull, ovf) && st == ST_OK) st = ST_EOVERFLOW;
+    if (lane == 0) {
+        I.bkz_tours = tours;
+        I.bkz_inserts = inserts;
+        I.bkz_nodes = nodes;
+        if (st != ST_OK) set_status(I, st);
+    }
 }
 
 // Fixed-point parameters of the exact integer filter used by the walkers

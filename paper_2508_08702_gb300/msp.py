@@ -37,7 +37,8 @@ class msp_opts(C.Structure):
                 ("warps_per_block", C.c_int), ("blocks_per_sm", C.c_int),
                 ("smem_tables", C.c_int), ("sol_capacity", C.c_int64), ("max_seconds", C.c_double),
                 ("donation_capacity", C.c_int64), ("log_features", C.c_int),
-                ("lds_budget", C.c_int), ("lds_max", C.c_int), ("first_split_target", C.c_int)]
+                ("lds_budget", C.c_int), ("lds_max", C.c_int), ("first_split_target", C.c_int),
+                ("bkz_beta", C.c_int), ("bkz_max_tours", C.c_int)]
 
 
 class msp_stats(C.Structure):
@@ -48,7 +49,8 @@ class msp_stats(C.Structure):
                 ("center_fma", C.c_int64), ("fallbacks", C.c_int64), ("donations", C.c_int64),
                 ("walker_util", C.c_double), ("first_ms", C.c_double), ("status", C.c_int32),
                 ("lds_budget", C.c_int32),
-                ("ms", C.c_double)]
+                ("ms", C.c_double), ("bkz_tours", C.c_int64), ("bkz_inserts", C.c_int64),
+                ("bkz_nodes", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -1,0 +1,138 @@
+"""Pins for the oracle's BKZ reduction of the kernel basis (Sec. 2: "LLL or
+blockwise Korkine-Zolotarev reduction").
+
+Checked against things the C code does not compute itself:
+  * the reduced basis spans the same lattice: an integer matrix U with
+    |det U| = 1 maps the LLL basis onto it (exact integer arithmetic here);
+  * Gram-Schmidt volume is preserved (product of B_i = det of the Gram
+    matrix, by exact Bareiss elimination);
+  * BKZ-reducedness: in every block the first projected vector is within
+    delta of the block's shortest nonzero projected vector, found here by an
+    independent exact-rational search on small lattices;
+  * with beta = dd the first vector is a shortest vector of the lattice;
+  * enumeration on the BKZ basis finds the brute-force solution set.
+"""
+from fractions import Fraction
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import definition as DEF
+from oracle import oracle as O
+from paper_2508_08702_gb300 import instances as I
+
+CASES = [I.small(1000 + s, m, n, D) for s in range(3)
+         for (m, n, D) in [(2, 18, 12), (3, 20, 8), (4, 22, 6), (3, 21, 100)]]
+
+
+def bareiss_det(M):
+    A = [[int(x) for x in row] for row in M]
+    n = len(A)
+    sign, prev = 1, 1
+    for k in range(n - 1):
+        if A[k][k] == 0:
+            for i in range(k + 1, n):
+                if A[i][k] != 0:
+                    A[k], A[i] = A[i], A[k]
+                    sign = -sign
+                    break
+            else:
+                return 0
+        for i in range(k + 1, n):
+            for j in range(k + 1, n):
+                A[i][j] = (A[i][j] * A[k][k] - A[i][k] * A[k][j]) // prev
+        prev = A[k][k]
+    return sign * A[-1][-1]
+
+
+def exact_gso(b):
+    b = [[int(v) for v in row] for row in b]
+    dd = len(b)
+    G = [[sum(x * y for x, y in zip(b[i], b[j])) for j in range(dd)] for i in range(dd)]
+    mu = [[Fraction(0)] * dd for _ in range(dd)]
+    B = [Fraction(0)] * dd
+    for i in range(dd):
+        for j in range(i):
+            mu[i][j] = (G[i][j] - sum(mu[j][q] * mu[i][q] * B[q] for q in range(j))) / B[j]
+        B[i] = Fraction(G[i][i]) - sum(mu[i][q] ** 2 * B[q] for q in range(i))
+    return mu, B
+
+
+def block_shortest(mu, B, k, h):
+    """Squared length of the shortest nonzero vector of the projected block
+    [k, h), by exact Fincke-Pohst search (rational arithmetic)."""
+    best = B[k]
+    n = h - k
+    u = [0] * n
+
+    def rec(t, rho):
+        nonlocal best
+        c = -sum(u[i] * mu[k + i][k + t] for i in range(t + 1, n))
+        # all integers x with rho + (x - c)^2 B <= best
+        import math
+        span = (best - rho) / B[k + t]
+        if span < 0:
+            return
+        r = Fraction(math.isqrt(int(span.numerator // span.denominator) + 1) + 1)
+        lo, hi = int(c - r) - 1, int(c + r) + 1
+        for x in range(lo, hi + 1):
+            d = rho + (x - c) ** 2 * B[k + t]
+            if d > best:
+                continue
+            u[t] = x
+            if t == 0:
+                if any(u) and d < best:
+                    best = d
+            else:
+                rec(t - 1, d)
+            u[t] = 0
+
+    rec(n - 1, Fraction(0))
+    return best
+
+
+@pytest.mark.parametrize("inst", CASES, ids=lambda x: x.tag)
+@pytest.mark.parametrize("beta", [4, 10])
+def test_same_lattice_and_volume(inst, beta):
+    _, kern, _ = O.reduce(inst.A, inst.d)
+    r = O.bkz(kern, beta)
+    kb = r.kern.astype(np.int64)
+    U = np.rint(kb.astype(float) @ np.linalg.pinv(kern.astype(float))).astype(np.int64)
+    assert np.array_equal(U @ kern.astype(np.int64), kb)
+    assert abs(bareiss_det(U)) == 1
+    G0 = kern.astype(object) @ kern.astype(object).T
+    G1 = kb.astype(object) @ kb.astype(object).T
+    assert bareiss_det(G0) == bareiss_det(G1)
+
+
+@pytest.mark.parametrize("inst", CASES[:4], ids=lambda x: x.tag)
+def test_blocks_are_reduced(inst):
+    beta, delta = 4, 0.99
+    _, kern, _ = O.reduce(inst.A, inst.d)
+    kb = O.bkz(kern, beta, delta=delta).kern
+    mu, B = exact_gso(kb)
+    dd = len(B)
+    for k in range(dd - 1):
+        h = min(k + beta, dd)
+        lam = block_shortest(mu, B, k, h)
+        assert delta * float(B[k]) <= float(lam) * (1 + 1e-12), k
+
+
+def test_full_block_gives_a_shortest_vector():
+    inst = I.small(1001, 2, 12, 6)
+    _, kern, _ = O.reduce(inst.A, inst.d)
+    dd = kern.shape[0]
+    kb = O.bkz(kern, dd, delta=0.999999).kern
+    mu, B = exact_gso(kb)
+    lam = block_shortest(mu, B, 0, dd)
+    assert float(B[0]) <= float(lam) / 0.999999 * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("inst", CASES, ids=lambda x: x.tag)
+def test_enumeration_on_bkz_basis_finds_every_solution(inst):
+    _, kern, _ = O.reduce(inst.A, inst.d)
+    kb = O.bkz(kern, 10).kern
+    g = O.gso(kb)
+    r = O.enumerate(kb, g, inst.A, inst.d)
+    assert np.array_equal(r.solutions, DEF.brute_force(inst.A, inst.d))
