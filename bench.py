@@ -49,7 +49,110 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--instances", type=int, default=64,
                    help="run only the first K instances of the batch (small profiling cases)")
+    p.add_argument("--workload", default="batch64", choices=["batch64"] + sorted(WORKLOADS),
+                   help="batch64: the nodes/s benchmark; the others time the paper's all- and "
+                        "first-solution configurations once (one GPU)")
+    p.add_argument("--bkz", type=int, default=None, help="BKZ block size (default: 0 for batch64, 10 otherwise)")
+    p.add_argument("--cap", type=float, default=None, help="time cap in seconds for the other workloads")
+    p.add_argument("--orders", default="plain,learned,lds", help="first-solution workloads: orders to time")
     return p.parse_args()
+
+
+# The paper's larger configurations (synthetic stand-ins, seeds in instances.py):
+# name -> (generator, mode, default time cap in seconds)
+WORKLOADS = {
+    "m8_all": ("m8_n70", "all", 300.0),     # m=8, n=70, D=200, 16 instances
+    "m9_all": ("m9_n80", "all", 1200.0),    # m=9, n=80, D=100, 8 instances, 40 ones planted
+    "m8_first": ("m8_n70", "first", 120.0),
+    "m12_first": ("m12_n110", "first", 60.0),   # m=12, n=110, D=100, 4 instances
+}
+
+
+def extended(args):
+    """One timed run of a paper configuration: wall time from the reduction
+    to the verified solutions (the paper's timings include the reduction),
+    per instance and for the batch; first-solution workloads compare the
+    queue orders."""
+    import numpy as np
+    import torch
+    from paper_2508_08702_gb300 import build as B
+    from paper_2508_08702_gb300 import instances as I
+    from paper_2508_08702_gb300 import learn
+    from paper_2508_08702_gb300 import msp as M
+
+    B.build()
+    gen, mode, cap = WORKLOADS[args.workload]
+    cap = args.cap or cap
+    bkz = 10 if args.bkz is None else args.bkz
+    insts = getattr(I, gen)()
+    pk = I.pack(insts)
+    opts = dict(bkz_beta=bkz, max_seconds=cap + 60)
+    if args.lanes:
+        opts["lanes"] = args.lanes
+    out = {"workload": args.workload, "instances": len(insts), "m": insts[0].m, "n": insts[0].n, "D": insts[0].D,
+           "bkz_beta": bkz, "cap_s": cap, "data": "synthetic (planted instances of the paper's shapes)",
+           "gpu": torch.cuda.get_device_name()}
+    clocks = Clocks(torch.cuda.current_device())
+
+    def verified(ctx, i, inst):
+        xs = ctx.msp_solutions(i).astype(np.int64)
+        ok = all(np.array_equal(x @ inst.A.T.astype(np.int64), inst.d) for x in xs)
+        return ok, any(np.array_equal(inst.planted, x) for x in xs), len(xs)
+
+    if mode == "all":
+        ctx = M.Context(**opts)
+        ctx.msp_build_lattice(pk.dims, pk.A, pk.d)
+        torch.cuda.synchronize()
+        clocks.start()
+        t0 = time.perf_counter()
+        ctx.msp_reduce()
+        res = ctx.msp_enumerate(M.MSP_ALL, M.MSP_PLAIN, cap, allow=(M.MSP_OK, M.MSP_ETIMEOUT))
+        wall = time.perf_counter() - t0
+        out["clocks"] = clocks.stop()
+        ph = ctx.msp_phase_ms()
+        checks = [verified(ctx, i, x) for i, x in enumerate(insts)]
+        out.update({"metric": "time to all solutions (reduction + enumeration), whole batch", "value": wall,
+                    "unit": "s", "higher_is_better": False, "complete": res.status == M.MSP_OK,
+                    "status": res.status, "lanes": ctx.lanes, "phase_ms": {k: round(v, 1) for k, v in ph.items()},
+                    "nodes": res.total["nodes"], "nodes_per_s": res.total["nodes"] / (ph["enumerate"] / 1e3),
+                    "solutions": [c[2] for c in checks], "all_verified": all(c[0] for c in checks),
+                    "planted_found": sum(c[1] for c in checks)})
+        ctx.close()
+    else:
+        theta = None
+        if "learned" in args.orders:
+            t0 = time.perf_counter()
+            data = learn.collect(I.training_set(256))
+            theta, _ = learn.train(data, steps=4000)
+            out["scorer_training_s"] = round(time.perf_counter() - t0, 2)
+        names = {"plain": M.MSP_PLAIN, "learned": M.MSP_LEARNED, "lds": M.MSP_LDS}
+        runs = {}
+        clocks.start()
+        for name in args.orders.split(","):
+            ctx = M.Context(**opts)
+            if name == "learned":
+                ctx.msp_set_scorer(theta)
+            ctx.msp_build_lattice(pk.dims, pk.A, pk.d)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.msp_reduce()
+            res = ctx.msp_enumerate(M.MSP_FIRST, names[name], cap, allow=(M.MSP_OK, M.MSP_ETIMEOUT))
+            wall = time.perf_counter() - t0
+            ph = ctx.msp_phase_ms()
+            fm = [s["first_ms"] for s in res.stats]
+            solved = [f for f in fm if f >= 0]
+            checks = [verified(ctx, i, x) for i, x in enumerate(insts)]
+            runs[name] = {"wall_s": round(wall, 3), "reduce_ms": round(ph["reduce"], 1),
+                          "solved": len(solved), "first_ms": [round(f, 1) for f in fm],
+                          "median_first_ms": float(np.median(fm)) if len(solved) == len(fm) else None,
+                          "nodes": res.total["nodes"], "all_verified": all(c[0] for c in checks)}
+            ctx.close()
+        out["clocks"] = clocks.stop()
+        med = [r["median_first_ms"] for r in runs.values() if r["median_first_ms"] is not None]
+        out.update({"metric": "median time to an instance's first solution (from the enumeration start), "
+                              "best queue order", "value": min(med) / 1e3 if med else None, "unit": "s",
+                    "higher_is_better": False, "orders": runs})
+    print(json.dumps(out), flush=True)
 
 
 # --------------------------------------------------------------------------
@@ -213,6 +316,10 @@ def main():
     if args.impl == "reference":
         reference_arm(args, rank, world)
         return
+    if args.workload != "batch64":
+        if rank == 0:
+            extended(args)
+        return
     import numpy as np
     import torch
     from paper_2508_08702_gb300 import build as B
@@ -227,7 +334,6 @@ def main():
     pk = I.pack(insts)
     kw = {} if args.lanes is None else {"lanes": args.lanes}
     ctx = M.Context(**kw)
-    lanes = ctx.opts.lanes
     A_dev = torch.from_numpy(pk.A).to(dev)
     d_dev = torch.from_numpy(pk.d).to(dev)
     A_pin = torch.from_numpy(pk.A).pin_memory()
@@ -243,6 +349,7 @@ def main():
         step_device()
         ctx.msp_wait()
     peak_dfma = ctx.msp_fp64_peak()
+    lanes = ctx.lanes   # in effect for this batch (automatic unless --lanes)
 
     # ---- device-timed steps, inputs resident in HBM ----
     clocks = Clocks(local)

@@ -79,9 +79,11 @@ typedef struct {
     int sym;               /* [1] 1: enumerate one of v, -v (first nonzero u > 0);        */
                            /*     0: both signs, keep leaves whose last entry is +1       */
     int use_eps;           /* [1] slack eps = (n+1) 2^-20 on both tests (0: none)         */
-    int lanes;             /* [8] lanes per subtree walker: 4, 8, 16 or 32.  Also fixes the */
-                           /*      summation order of ||w||_1 (G interleaved partial sums */
-                           /*      combined pairwise), so node counts depend on it        */
+    int lanes;             /* [0] lanes per subtree walker: 4, 8, 16 or 32; 0 picks 8 when */
+                           /*     the widest instance of the batch has n + 1 <= 64, else  */
+                           /*     16 (msp_lanes tells the choice).  Also fixes the        */
+                           /*     summation order of ||w||_1 (G interleaved partial sums  */
+                           /*     combined pairwise), so node counts depend on it         */
     int split_depth;       /* [24] maximum number of top levels the splitter expands      */
     int split_target;      /* [0] stop splitting once an instance has this many subtree   */
                            /*     prefixes (0: 8 x the number of walkers / instances)     */
@@ -202,6 +204,10 @@ MSP_API msp_status msp_run_async(msp_ctx *ctx, int mode, int order);
  * MSP_ESTATE until the next capture). */
 MSP_API msp_status msp_graph_capture(msp_ctx *ctx, int mode, int order);
 MSP_API msp_status msp_graph_launch(msp_ctx *ctx);
+
+/* Lanes per walker in effect for the current batch (0 before
+ * msp_build_lattice). */
+MSP_API int msp_lanes(const msp_ctx *ctx);
 
 /* Synchronise and read the statistics of the last msp_run_async(). */
 MSP_API msp_status msp_wait(msp_ctx *ctx, msp_stats *stats, msp_stats *total);

@@ -61,6 +61,7 @@ struct msp_ctx {
     msp_opts o;
     cudaStream_t st = nullptr;
     int dev = 0, sms = 0, smem_optin = 48 * 1024;
+    int lanes = 8;                       // lanes per walker for the current batch
     std::string err;
     int64_t launches = 0;
     int state = 0;   // 0 empty, 1 lattice built, 2 reduced, 3 enumerated
@@ -190,16 +191,16 @@ void refresh_pools(msp_ctx* c) {
     P.ctrl = ptr<Ctrl>(c->ctrl);
 }
 
-int walkers_of(const msp_ctx* c, int blocks, int threads) { return blocks * threads / c->o.lanes; }
+int walkers_of(const msp_ctx* c, int blocks, int threads) { return blocks * threads / c->lanes; }
 
 // Threads per enumeration block: the requested warps, reduced while the
 // walkers' level state would not fit the shared memory a block may use.
 void enum_launch_shape(const msp_ctx* c, int* blocks, int* threads) {
     int t = c->o.warps_per_block * 32;
-    while (t > 32 && enum_smem_bytes(c->o.lanes, t, c->Kmax) > c->smem_optin) t -= 32;
+    while (t > 32 && enum_smem_bytes(c->lanes, t, c->Kmax) > c->smem_optin) t -= 32;
     *threads = t;
     int bps = c->o.blocks_per_sm;
-    if (bps <= 0) bps = std::max(1, enum_blocks_per_sm(c->o.lanes, t, c->dimMax, c->Kmax));
+    if (bps <= 0) bps = std::max(1, enum_blocks_per_sm(c->lanes, t, c->dimMax, c->Kmax));
     *blocks = c->sms * bps;
 }
 
@@ -274,7 +275,7 @@ void msp_default_opts(msp_opts* o) {
     o->hoelder = 0;
     o->sym = 1;
     o->use_eps = 1;
-    o->lanes = 8;
+    o->lanes = 0;
     o->split_depth = 24;
     o->split_target = 0;
     o->split_capacity = 0;
@@ -321,7 +322,7 @@ msp_status msp_create(msp_ctx** out, const msp_opts* opts, void* stream) {
     if (opts) c->o = *opts; else msp_default_opts(&c->o);
     const msp_opts& o = c->o;
     if (o.N < 1 || o.N > (1LL << 30) || !(o.delta > 0.25 && o.delta < 1.0) || !(o.eta >= 0.5 && o.eta < 1.0) ||
-        o.hoelder < 0 || o.hoelder > 2 || (o.lanes != 4 && o.lanes != 8 && o.lanes != 16 && o.lanes != 32) ||
+        o.hoelder < 0 || o.hoelder > 2 || (o.lanes != 0 && o.lanes != 4 && o.lanes != 8 && o.lanes != 16 && o.lanes != 32) ||
         o.split_depth < 0 || o.warps_per_block < 1 || o.warps_per_block > 8 || o.sol_capacity < 1 ||
         o.lll_max_iter < 1 || !(o.max_seconds > 0.0) || o.donation_capacity < 0 || o.lds_budget < -1 ||
         o.lds_budget > 127 || o.lds_max < 0 || o.lds_max > 127 || o.first_split_target < 0 ||
@@ -396,6 +397,9 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     c->Kmax = Kmax;
     c->dimMax = dimMax;
     c->dimPad = (dimMax + 31) / 32 * 32;
+    // automatic lanes: at most 8 coordinates per lane on 8-lane walkers,
+    // else 16-lane walkers (wider lattices spill registers at 8 lanes)
+    c->lanes = c->o.lanes ? c->o.lanes : (dimMax <= 64 ? 8 : 16);
     int64_t nBq = 0;
     for (int i = 0; i < count; ++i) {
         h[i].offBq = nBq;
@@ -522,7 +526,7 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
     ++c->launches;
     Pools Ps = c->P;
     Ps.skip = lds >= 0 ? ptr<unsigned char>(c->skip) : nullptr;
-    if ((e = launch_split(Ps, cfg, c->o.lanes, c->o.split_depth, target, ptr<int64_t>(c->fcnt), c->st)) !=
+    if ((e = launch_split(Ps, cfg, c->lanes, c->o.split_depth, target, ptr<int64_t>(c->fcnt), c->st)) !=
         cudaSuccess)
         return cuda_fail(c, e, "split");
     c->launches += 2;
@@ -557,7 +561,7 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
         Pq.qperm = ptr<int64_t>(c->perm);
     }
     if (!cont) record(c, c->evs1);
-    if ((e = launch_enum(Pq, cfg, c->o.lanes, blocks, threads, ptr<char>(c->scratch), c->Kmax, c->dimPad, c->st)) !=
+    if ((e = launch_enum(Pq, cfg, c->lanes, blocks, threads, ptr<char>(c->scratch), c->Kmax, c->dimPad, c->st)) !=
         cudaSuccess)
         return cuda_fail(c, e, "enumerate");
     ++c->launches;
@@ -781,6 +785,8 @@ msp_status msp_enumerate(msp_ctx* c, int mode, int order, double time_cap_s, msp
     if (s != MSP_OK) return s;
     return msp_wait(c, stats, total);
 }
+
+int msp_lanes(const msp_ctx* c) { return (c && c->state >= 1) ? c->lanes : 0; }
 
 int msp_mlp_param_count(void) { return mlp_param_count(); }
 

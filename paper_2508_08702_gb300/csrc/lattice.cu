@@ -53,6 +53,23 @@ __device__ __forceinline__ int64_t dot_exact(const int64_t* __restrict__ a, cons
     return (int64_t)s;
 }
 
+// The same exact dot product when every entry is below 2^24 in magnitude
+// (small != 0): 128 products of 48 bits sum below 2^55, so int64 is exact.
+__device__ __forceinline__ int64_t dot_small(const int64_t* __restrict__ a, const int64_t* __restrict__ b, int L,
+                                             bool small, bool& ovf) {
+    if (!small || L > 128) return dot_exact(a, b, L, ovf);
+    int64_t s = 0;
+    for (int c = 0; c < L; ++c) s += a[c] * b[c];
+    return s;
+}
+
+// warp-uniform: are all entries of rows [r0, r1) below 2^24 in magnitude?
+__device__ __forceinline__ bool rows_small(const int64_t* __restrict__ b, int r0, int r1, int L) {
+    bool ok = true;
+    for (int e = (threadIdx.x & 31) + r0 * L; e < r1 * L; e += 32) ok &= (b[e] < (1 << 24) && b[e] > -(1 << 24));
+    return __all_sync(kFull, ok);
+}
+
 __device__ __forceinline__ double pick4(const double (&a)[4], int q) {
     return q == 0 ? a[0] : q == 1 ? a[1] : q == 2 ? a[2] : a[3];
 }
@@ -99,31 +116,37 @@ __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ 
 // warp: exact Gram matrix G (K x K), FP64 Gram-Schmidt rows recomputed from
 // it (mu, r: K x K; invB, B: K), lazy size reduction, Lovasz swaps.
 // Returns a status; iterations and swaps are added to the counters.
+//
+// Restart (k0 > 0): G is the Gram matrix of the current basis and rows
+// 0 .. k0-1 are an LLL fixed point whose Gram-Schmidt rows (mu, r, invB, B)
+// are in place -- a run from scratch would pass them unchanged, so starting
+// at k0 gives the same result.  *lo receives the lowest row changed.
 __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, double* __restrict__ mu,
                             double* __restrict__ r, double* __restrict__ invB, double* __restrict__ B, int K, int L,
                             double delta, double eta, int64_t max_iter, unsigned long long deadline_ns,
-                            int64_t& iters, int64_t& swaps) {
+                            int64_t& iters, int64_t& swaps, int k0 = 0, int* lo = nullptr) {
     const int lane = threadIdx.x & 31;
     auto mu_at = [&](int j, int i) { return mu[(int64_t)j * K + i]; };
     int32_t st = ST_OK;
     int64_t it = 0;
-    // exact Gram matrix
-    {
+    int low = K;
+    bool small = rows_small(b, 0, K, L);
+    if (k0 <= 0) {   // exact Gram matrix
         bool ovf = false;
         for (int e = lane; e < K * K; e += 32) {
             const int i = e / K, j = e % K;
             if (j <= i) {
-                const int64_t g = dot_exact(b + (int64_t)i * L, b + (int64_t)j * L, L, ovf);
+                const int64_t g = dot_small(b + (int64_t)i * L, b + (int64_t)j * L, L, small, ovf);
                 G[(int64_t)i * K + j] = g;
                 G[(int64_t)j * K + i] = g;
             }
         }
         if (__any_sync(kFull, ovf)) st = ST_EOVERFLOW;
         __syncwarp();
+        if (st == ST_OK) gso_row_warp(0, G, mu_at, B, r, mu, &B[0], lane, invB);
     }
-    if (st == ST_OK) gso_row_warp(0, G, mu_at, B, r, mu, &B[0], lane, invB);
 
-    int k = 1;
+    int k = k0 > 1 ? k0 : 1;
     while (st == ST_OK && k < K) {
         if (++it > max_iter) { st = ST_ECAP; break; }
         if ((it & 255) == 0) {   // device-clock safety cap (uniform across the warp)
@@ -160,8 +183,10 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
             }
             if (__any_sync(kFull, ovf)) { st = ST_EOVERFLOW; break; }
             if (!changed) break;
+            low = min(low, k);
+            small = small && rows_small(b, k, k + 1, L);
             for (int i = lane; i < K; i += 32) {
-                const int64_t g = dot_exact(b + (int64_t)k * L, b + (int64_t)i * L, L, ovf);
+                const int64_t g = dot_small(b + (int64_t)k * L, b + (int64_t)i * L, L, small, ovf);
                 G[(int64_t)k * K + i] = g;
                 G[(int64_t)i * K + k] = g;
             }
@@ -193,6 +218,7 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
             }
             __syncwarp();
             ++swaps;
+            low = min(low, k - 1);
             if (k - 1 == 0) gso_row_warp(0, G, mu_at, B, r, mu, &B[0], lane, invB);
             k = (k > 1) ? k - 1 : 1;
         } else {
@@ -200,6 +226,7 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
         }
     }
     iters += it;
+    if (lo) *lo = low;
     return st;
 }
 
@@ -385,16 +412,20 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
     char* sp = S.base + (int64_t)blockIdx.x * S.stride;
     int64_t* b = reinterpret_cast<int64_t*>(sp);                 // dd x dim
     int64_t* rows = b + (int64_t)K * D;                           // block copy
-    int64_t* G = rows + (int64_t)K * D;                           // dd x dd
-    double* mu = reinterpret_cast<double*>(G + (int64_t)K * K);   // dd x dd
+    int64_t* G = rows + (int64_t)K * D;                           // dd x dd, exact Gram of b
+    double* mu = reinterpret_cast<double*>(G + (int64_t)K * K);   // Eq. (4) rows (divided form)
     double* r = mu + (int64_t)K * K;
-    double* invB = r + (int64_t)K * K;
-    double* B = invB + K;
-    double* yv = B + K;                                           // SVP: centre per level
+    double* mu2 = r + (int64_t)K * K;                             // the LLL's rows (reciprocal form)
+    double* r2 = mu2 + (int64_t)K * K;
+    double* B = r2 + (int64_t)K * K;
+    double* invB2 = B + K;
+    double* B2 = invB2 + K;
+    double* yv = B2 + K;                                          // SVP: centre per level
     double* rhoP = yv + K;                                        // SVP: parent norm per level
     int64_t* a = reinterpret_cast<int64_t*>(rhoP + K);
-    double* Bsvp = reinterpret_cast<double*>(a + K);              // unused slot kept for alignment
-    int32_t* u = reinterpret_cast<int32_t*>(Bsvp + K);
+    double* spare = reinterpret_cast<double*>(a + K);
+    double* spare2 = spare + K;
+    int32_t* u = reinterpret_cast<int32_t*>(spare2 + K);
     int32_t* best = u + K;
     int32_t* u1v = best + K;
     int32_t* ziv = u1v + K;
@@ -407,29 +438,37 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
     __syncwarp();
     int32_t st = ST_OK;
     int64_t tours = 0, inserts = 0, nodes = 0, iters = 0, swaps = 0;
+    bool small = rows_small(b, 0, dd, dim);
+    {   // exact Gram matrix; kept up to date row by row below
+        bool ovf = false;
+        for (int e = lane; e < dd * dd; e += 32) {
+            const int i = e / dd, j = e % dd;
+            if (j <= i) {
+                const int64_t g = dot_small(b + (int64_t)i * dim, b + (int64_t)j * dim, dim, small, ovf);
+                G[(int64_t)i * dd + j] = g;
+                G[(int64_t)j * dd + i] = g;
+            }
+        }
+        if (__any_sync(kFull, ovf)) st = ST_EOVERFLOW;
+        __syncwarp();
+    }
+    int gso_lo = 0;          // Eq. (4) rows gso_lo .. dd-1 are stale
+    bool lll_state = false;  // mu2, r2, invB2, B2 hold an LLL fixed point of b
     for (int tour = 0; tour < max_tours && st == ST_OK; ++tour) {
         ++tours;
         bool inserted = false;
         for (int k = 0; k + 1 < dd && st == ST_OK; ++k) {
             const int h = min(k + beta, dd);
-            // Gram-Schmidt data of the current basis (exact Gram, divided mu)
-            bool ovf = false;
-            for (int e = lane; e < dd * dd; e += 32) {
-                const int i = e / dd, j = e % dd;
-                if (j <= i) {
-                    const int64_t g = dot_exact(b + (int64_t)i * dim, b + (int64_t)j * dim, dim, ovf);
-                    G[(int64_t)i * dd + j] = g;
-                    G[(int64_t)j * dd + i] = g;
-                }
+            // Gram-Schmidt rows of the changed part of the basis (Eq. (4), divided form)
+            if (gso_lo < dd) {
+                for (int i = gso_lo; i < dd; ++i)
+                    gso_row_warp(i, G + (int64_t)i * dd, mu_at, B, r + (int64_t)i * dd, mu + (int64_t)i * dd, &B[i],
+                                 lane);
+                bool badB = false;   // a level with B_t <= 0 would never end its zig-zag
+                for (int i = lane; i < dd; i += 32) badB |= !(B[i] > 0.0 && B[i] < 1e300);
+                if (__any_sync(kFull, badB)) { st = ST_EOVERFLOW; break; }
+                gso_lo = dd;
             }
-            if (__any_sync(kFull, ovf)) { st = ST_EOVERFLOW; break; }
-            __syncwarp();
-            for (int i = 0; i < dd; ++i)
-                gso_row_warp(i, G + (int64_t)i * dd, mu_at, B, r + (int64_t)i * dd, mu + (int64_t)i * dd, &B[i],
-                             lane);
-            bool badB = false;   // a level with B_t <= 0 would never end its zig-zag
-            for (int i = lane; i < dd; i += 32) badB |= !(B[i] > 0.0 && B[i] < 1e300);
-            if (__any_sync(kFull, badB)) { st = ST_EOVERFLOW; break; }
             // shortest nonzero vector of the projected block (lane 0)
             int found = 0;
             if (lane == 0) {
@@ -536,7 +575,26 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
             for (int e = lane; e < nb * dim; e += 32)
                 b[(int64_t)k * dim + e] = (a0 == -1 && e < dim) ? -rows[e] : rows[e];
             __syncwarp();
-            st = lll_warp(b, G, mu, r, invB, B, dd, dim, delta, 0.51, lll_max_iter, deadline, iters, swaps);
+            // Gram rows of the replaced block
+            small = small && rows_small(b, k, h, dim);
+            bool ovf = false;
+            for (int e = lane; e < nb * dd; e += 32) {
+                const int i = k + e / dd, j = e % dd;
+                const int64_t gv = dot_small(b + (int64_t)i * dim, b + (int64_t)j * dim, dim, small, ovf);
+                G[(int64_t)i * dd + j] = gv;
+                G[(int64_t)j * dd + i] = gv;
+            }
+            if (__any_sync(kFull, ovf)) { st = ST_EOVERFLOW; break; }
+            __syncwarp();
+            // LLL of the whole basis: once a first run has made the basis an
+            // LLL fixed point, the rows above k are untouched, so later runs
+            // restart at k
+            int lo = dd;
+            st = lll_warp(b, G, mu2, r2, invB2, B2, dd, dim, delta, 0.51, lll_max_iter, deadline, iters, swaps,
+                          lll_state ? k : 0, &lo);
+            lll_state = true;
+            small = rows_small(b, 0, dd, dim);
+            gso_lo = min(gso_lo, min(k, lo));
             ++inserts;
             inserted = true;
         }

@@ -98,6 +98,8 @@ def load():
     L.msp_reduce_lattice_noalloc.restype = C.c_int
     L.msp_graph_capture.argtypes = [P, C.c_int, C.c_int]
     L.msp_graph_capture.restype = C.c_int
+    L.msp_lanes.argtypes = [P]
+    L.msp_lanes.restype = C.c_int
     L.msp_graph_launch.argtypes = [P]
     L.msp_graph_launch.restype = C.c_int
     L.msp_mlp_param_count.argtypes = []
@@ -187,6 +189,12 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    @property
+    def lanes(self) -> int:
+        """Lanes per walker in effect for the current batch (fixes the
+        |w|_1 summation order, hence the node counts)."""
+        return int(self._L.msp_lanes(self._h))
 
     @property
     def kernel_launches(self) -> int:

@@ -42,7 +42,7 @@ def test_host_only_entry_points(lib):
     from paper_2508_08702_gb300 import msp
     o = msp.msp_opts()
     lib.msp_default_opts(ctypes.byref(o))
-    assert (o.N, o.lanes, o.sym, o.hoelder, o.use_eps) == (1024, 8, 1, 0, 1)
+    assert (o.N, o.lanes, o.sym, o.hoelder, o.use_eps) == (1024, 0, 1, 0, 1)
     assert abs(o.delta - 0.99) < 1e-15
     lib.msp_status_string.restype = ctypes.c_char_p
     assert lib.msp_status_string(0) == b"ok"

@@ -107,7 +107,7 @@ def test_learned_order_keeps_all_mode_exact():
     for i, inst in enumerate(insts):
         assert r_learn.stats[i]["nodes"] == r_plain.stats[i]["nodes"]
         assert np.array_equal(s_learn[i], s_plain[i])
-        ref = O.solve(inst.A, inst.d, lanes=c1.opts.lanes).result
+        ref = O.solve(inst.A, inst.d, lanes=c1.lanes).result
         assert r_learn.stats[i]["nodes"] == ref.nodes
     c1.close()
     c2.close()

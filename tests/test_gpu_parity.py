@@ -126,7 +126,7 @@ def test_full_batch_in_bench_configuration():
     large instances matches the oracle node for node."""
     insts = I.batch_m4_7(64)
     res, sols, ctx = run_gpu(insts)
-    lanes = ctx.opts.lanes
+    lanes = ctx.lanes
     rng = np.random.default_rng(0)
     for i, inst in enumerate(insts):
         x = sols[i].astype(np.int64)
@@ -198,7 +198,7 @@ def test_edge_cases():
     for i, x in enumerate(insts):
         want = DEF.brute_force(x.A, x.d)
         assert np.array_equal(sols[i], want), i
-        ref = O.solve(x.A, x.d, lanes=ctx.opts.lanes).result
+        ref = O.solve(x.A, x.d, lanes=ctx.lanes).result
         assert res.stats[i]["nodes"] == ref.nodes, i
     ctx.close()
 
