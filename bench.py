@@ -34,6 +34,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "enum nodes/s; time to all sols (m=9) & first sol (m=12), learned vs plain order"
+DRAM_BYTES_PER_NODE = (113.761024e6 + 465.414144e6) / 268321291   # enum_kernel<8, 8>, ncu
 UNIT = "nodes/s"
 WORKLOAD = "batch of 64 fMSP instances, m~U{4..7}, n=10(m-1), D in {50,100,200}, all solutions"
 
@@ -405,9 +406,17 @@ def main():
     res, ph = last
     ops = algorithmic_fp64_ops(res.stats, pk.dims, lanes)
     achieved = ops / (ph["enumerate"] / 1e3)
+    # DRAM bytes per launch: ncu's dram read + write per evaluated node on a
+    # 4-instance capture of the same kernel (profiles/enum_kernel_batch4.md),
+    # scaled by this launch's nodes
+    traffic = None
+    if lanes == 8:
+        traffic = DRAM_BYTES_PER_NODE * res.total["nodes"]
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_dfma / 1e9,
-            "unit": "Gop/s (FP64 lane ops)", "frac": achieved / peak_dfma, "traffic": None,
-            "peak_source": "measured FP64 fma throughput (msp_fp64_peak) on this GPU"}
+            "unit": "Gop/s (FP64 lane ops)", "frac": achieved / peak_dfma, "traffic": traffic,
+            "traffic_source": "ncu dram bytes per node of a 4-instance capture, scaled by nodes",
+            "peak_source": "measured FP64 fma throughput (msp_fp64_peak) on this GPU; the nominal "
+                           "GB300 FP64 rate 1.25 TFLOP/s is 625 G fma/s"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -54,7 +54,12 @@
  *         |w|_1: G interleaved partial sums s_l = sum_{c = l mod G} |w_c|
  *               (ascending c), then pairwise s_l += s_{l+off}, off = G/2..1.
  *       G ("lanes") is a parameter; G = 1 is the sequential sum.
- *   R10 Limited discrepancy search (Sec. 3, after Harvey and Ginsberg): a
+ *   R10 N = 2^10 (Sec. 2); delta = 0.99, eta = 0.51 (the paper gives neither);
+ *       inside LLL mu_kj = r_kj (1/B_j) with the reciprocal formed once per
+ *       row, in the enumeration tables mu = r / B (Eq. (4) as written).
+ *   R11 Instances are made feasible by a planted binary x, d = A x (the
+ *       construction of the paper's instance library is not described).
+ *   R12 Limited discrepancy search (Sec. 3, after Harvey and Ginsberg): a
  *       discrepancy is a level where u_t differs from the heuristic first
  *       value u^1 of that level's walk (the rounded centre; 0 on the
  *       all-zero levels of sym mode), whatever its rank in the zig-zag.
@@ -320,7 +325,7 @@ typedef struct {
     int sub_level;      /* >= 0: enumerate only the subtree below a prefix whose */
                         /* values u[sub_level+1 .. dd-1] are given; -1: off       */
     int lds;            /* >= 0: one limited-discrepancy iteration with this     */
-                        /* budget (R10); -1: plain depth-first search            */
+                        /* budget (R12); -1: plain depth-first search            */
 } oracle_enum_opts;
 
 typedef struct {
@@ -420,7 +425,7 @@ static void enum_level(enum_state *e, int t, const double *wp, double rho_p, int
     long u = u1;
 
     for (;;) {
-        if (e->o.lds >= 0 && u != u1 && disc + 1 > e->o.lds) {   /* budget spent (R10) */
+        if (e->o.lds >= 0 && u != u1 && disc + 1 > e->o.lds) {   /* budget spent (R12) */
             e->s.lds_cuts++;
             return;
         }
@@ -531,7 +536,7 @@ int oracle_enumerate(int dd, int dim, const double *mu, const double *B, const d
 /* ------------------------------------------------------------------------ */
 /* 6. BKZ-beta on the kernel basis (Sec. 2 names "LLL or blockwise           */
 /* Korkine-Zolotarev reduction" for step 1; the paper gives no parameters).  */
-/* Readings (R13):                                                           */
+/* Readings (R14):                                                           */
 /*   - BKZ runs on the kept kernel basis after LLL and extraction (the same */
 /*     lattice the enumeration walks; the rows scaled by N play no part).   */
 /*   - A tour visits k = 0 .. dd-2 with the block [k, h), h = min(k+beta,   */
@@ -655,7 +660,7 @@ int oracle_bkz(int dd, int dim, int64_t *b, int beta, double delta, int max_tour
             svp_level(&e, h - 1, 0.0);
             nodes += e.nodes;
             if (!e.found) continue;
-            /* insertion by unimodular row steps (R13) */
+            /* insertion by unimodular row steps (R14) */
             memcpy(rows, b + (size_t)k * dim, sizeof(int64_t) * (size_t)(h - k) * dim);
             for (int i = k; i < h; ++i) a[i - k] = best[i];
             for (int i = h - k - 1; i > 0; --i) {

@@ -140,7 +140,7 @@ class BKZResult:
 
 def bkz(kern: np.ndarray, beta: int, delta: float = 0.99, max_tours: int = 16,
         lll_max_iter: int = 50_000_000) -> BKZResult:
-    """BKZ-beta of the kernel basis (Sec. 2; readings in the C file, R13)."""
+    """BKZ-beta of the kernel basis (Sec. 2; readings in the C file, R14)."""
     b = np.ascontiguousarray(kern, dtype=np.int64).copy()
     dd, dim = b.shape
     t = np.zeros(1, np.int64)
