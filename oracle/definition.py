@@ -4,6 +4,8 @@ fMSP (Sec. 1): the set {x in {0,1}^n : A x = d}.  Two exact ways to list it,
 neither of which uses lattices:
 
 * ``brute_force``  -- try all 2^n binary vectors (n <= 26);
+* ``brute_force_bounds`` -- the general problem of Sec. 2 with bounds
+  0 <= x_j <= r_j: try every point of the box (at most 2^22 points);
 * ``meet_in_middle`` -- split the columns in two halves, list all 2^(n/2)
   partial sums of each half, and join the halves whose sums add up to d
   (Horowitz-Sahni style).  Exact: every candidate pair is verified on the
@@ -80,3 +82,28 @@ def solutions(A: np.ndarray, d: np.ndarray) -> np.ndarray:
     """The solution set by whichever exact method fits the size."""
     n = np.asarray(A).shape[1]
     return brute_force(A, d) if n <= 22 else meet_in_middle(A, d)
+
+
+def brute_force_bounds(A: np.ndarray, d: np.ndarray, r: np.ndarray, chunk: int = 1 << 18) -> np.ndarray:
+    """All integer x with A x = d and 0 <= x <= r (mixed-radix counting)."""
+    A = np.asarray(A, dtype=np.int64)
+    d = np.asarray(d, dtype=np.int64)
+    r = np.asarray(r, dtype=np.int64)
+    m, n = A.shape
+    radix = r + 1
+    total = int(np.prod(radix))
+    if total > (1 << 22):
+        raise ValueError("the box has more than 2^22 points")
+    found = []
+    for start in range(0, total, chunk):
+        idx = np.arange(start, min(total, start + chunk), dtype=np.int64)
+        X = np.zeros((len(idx), n), np.int64)
+        rest = idx.copy()
+        for c in range(n):
+            X[:, c] = rest % radix[c]
+            rest //= radix[c]
+        ok = np.all(X @ A.T == d[None, :], axis=1)
+        if ok.any():
+            found.append(X[ok])
+    x = np.concatenate(found) if found else np.zeros((0, n), np.int64)
+    return _sorted(x, n)

@@ -38,8 +38,11 @@
  *       rho > ||w||_1 + eps) so that FP64 rounding can never drop a solution
  *       (every solution sits exactly on both bounds).  eps = 0 is available.
  *   R5  Leaf: the integer vector v = sum u_j b_j is checked exactly
- *       (Theorem 1): last entry +-1 (sign-normalised to +1), all others +-1,
- *       then A x = d with x = (v + 1)/2.
+ *       (Theorem 1): last entry +-r_max (sign-normalised to +r_max), all
+ *       others in [-r_max, r_max], then A x = d with x_c = (v_c + r_max) /
+ *       (2 c_c); binary: r_max = c_c = 1, v = +-1, x = (v + 1)/2.  General
+ *       bounds: R = (n+1) r_max^2, the Hoelder bound is r_max ||w||_1 (the
+ *       product formed first, then the slack added).
  *   R6  Symmetry: v and -v are both lattice points.  In "sym" mode levels
  *       whose prefix above is all zero try u = 0, 1, 2, ... only (the first
  *       nonzero coefficient from the top is positive).  "literal" mode runs
@@ -85,16 +88,40 @@ enum { OR_OK = 0, OR_EOVERFLOW = 1, OR_ECAP = 2, OR_ENOMEM = 3, OR_EINVAL = 4 };
 #define OR_ENTRY_LIMIT ((int64_t)1 << 58)
 
 /* ------------------------------------------------------------------------ */
-/* 1. Lattice build (Sec. 2, Eq. (2)), binary bounds.                         */
+/* 1. Lattice build (Sec. 2, Eq. (2)).                                        */
+/* Bounds 0 <= x_j <= r_j (l = 0 after the substitution of Sec. 2);          */
+/* r_max = lcm(r_1..r_n), c_j = r_max / r_j; binary: r = NULL, all ones.     */
 /* The generator has m+n+1 rows and n+1 columns; column j is basis vector j.  */
 /* We store it as K = n+1 vectors of length L = m+n+1, vector-major:          */
-/*   vector 0   = (-N d_1..-N d_m, -1 (n times), +1)                          */
-/*   vector j   = (N a_1j..N a_mj, 2 e_j, 0),  j = 1..n                       */
+/*   vector 0   = (-N d_1..-N d_m, -r_max (n times), +r_max)                  */
+/*   vector j   = (N a_1j..N a_mj, 2 c_j e_j, 0),  j = 1..n                   */
 /* ------------------------------------------------------------------------ */
-int oracle_build_lattice(int m, int n, const int32_t *A, const int64_t *d,
-                         int64_t N, int64_t *basis)
+static int64_t gcd64(int64_t a, int64_t b)
+{
+    while (b) { int64_t t = a % b; a = b; b = t; }
+    return a;
+}
+
+/* r_max = lcm of the bounds (1 for r = NULL); 0 when a bound is below 1 or
+ * the lcm exceeds 2^20. */
+int64_t oracle_rmax(int n, const int32_t *r)
+{
+    int64_t l = 1;
+    if (!r) return 1;
+    for (int j = 0; j < n; ++j) {
+        if (r[j] < 1) return 0;
+        l = l / gcd64(l, r[j]) * r[j];
+        if (l > ((int64_t)1 << 20)) return 0;
+    }
+    return l;
+}
+
+int oracle_build_lattice_bounds(int m, int n, const int32_t *A, const int64_t *d, const int32_t *r,
+                                int64_t N, int64_t *basis)
 {
     if (m < 1 || n < 1 || N < 1) return OR_EINVAL;
+    const int64_t rmax = oracle_rmax(n, r);
+    if (rmax < 1) return OR_EINVAL;
     const int K = n + 1, L = m + n + 1;
     memset(basis, 0, sizeof(int64_t) * (size_t)K * (size_t)L);
     for (int i = 0; i < m; ++i) {
@@ -102,14 +129,20 @@ int oracle_build_lattice(int m, int n, const int32_t *A, const int64_t *d,
         if (v >= OR_ENTRY_LIMIT || v <= -OR_ENTRY_LIMIT) return OR_EOVERFLOW;
         basis[i] = (int64_t)v;
     }
-    for (int j = 0; j < n; ++j) basis[m + j] = -1;
-    basis[m + n] = 1;
+    for (int j = 0; j < n; ++j) basis[m + j] = -rmax;
+    basis[m + n] = rmax;
     for (int j = 1; j <= n; ++j) {
         int64_t *b = basis + (size_t)j * L;
         for (int i = 0; i < m; ++i) b[i] = N * (int64_t)A[(size_t)i * n + (j - 1)];
-        b[m + (j - 1)] = 2;
+        b[m + (j - 1)] = 2 * (rmax / (r ? r[j - 1] : 1));
     }
     return OR_OK;
+}
+
+int oracle_build_lattice(int m, int n, const int32_t *A, const int64_t *d,
+                         int64_t N, int64_t *basis)
+{
+    return oracle_build_lattice_bounds(m, n, A, d, NULL, N, basis);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -341,6 +374,8 @@ typedef struct {
     const double *mu, *B, *bhat;
     const int32_t *kb, *A;
     const int64_t *d;
+    const int32_t *r;   /* bounds (NULL: binary) */
+    int64_t rmax;
     oracle_enum_opts o;
     double Rb, eps;
     int32_t *u;
@@ -388,14 +423,18 @@ static int leaf_check(enum_state *e)
         for (int j = 0; j < dd; ++j) acc += (int64_t)e->u[j] * (int64_t)e->kb[(size_t)j * dim + c];
         v[c] = acc;
     }
+    /* Theorem 1: last entry r_max, all others in [-r_max, r_max];
+     * x_c = (v_c + r_max) / (2 c_c) */
+    const int64_t rmax = e->rmax;
     int64_t last = v[dim - 1];
     if (e->o.sym) {
-        if (last == -1) { for (int c = 0; c < dim; ++c) v[c] = -v[c]; last = 1; }
+        if (last == -rmax) { for (int c = 0; c < dim; ++c) v[c] = -v[c]; last = rmax; }
     }
-    if (last != 1) return 0;
+    if (last != rmax) return 0;
     for (int c = 0; c < n; ++c) {
-        if (v[c] != 1 && v[c] != -1) return 0;
-        e->xbuf[c] = (uint8_t)((v[c] + 1) / 2);
+        const int64_t cc = 2 * (rmax / (e->r ? e->r[c] : 1));
+        if (v[c] > rmax || v[c] < -rmax || (v[c] + rmax) % cc != 0) return 0;
+        e->xbuf[c] = (uint8_t)((v[c] + rmax) / cc);
     }
     for (int i = 0; i < m; ++i) {          /* independent verification A x = d */
         int64_t acc = 0;
@@ -440,7 +479,7 @@ static void enum_level(enum_state *e, int t, const double *wp, double rho_p, int
             for (int c = 0; c < dim; ++c) w[c] = fma(x, e->bhat[(size_t)t * dim + c], wp[c]);
             int fail = 0;
             if (e->o.hoelder != HOELDER_OFF) {
-                const double h = norm1(w, dim, e->o.lanes) + e->eps;
+                const double h = (double)e->rmax * norm1(w, dim, e->o.lanes) + e->eps;
                 fail = rho > h;                    /* second pruning condition */
             }
             if (fail && e->o.hoelder == HOELDER_CUT) {
@@ -481,21 +520,24 @@ static void enum_level(enum_state *e, int t, const double *wp, double rho_p, int
  * prefix_u: when o->sub_level >= 0, values u[sub_level+1..dd-1] (entries
  * below are ignored); w^{(sub_level+1)} and its norm are rebuilt from them
  * with the same operations the full enumeration performs on the way down. */
-int oracle_enumerate(int dd, int dim, const double *mu, const double *B, const double *bhat,
-                     const int32_t *kb, int m, int n, const int32_t *A, const int64_t *d,
-                     const oracle_enum_opts *o, const int32_t *prefix_u,
-                     uint8_t *sol, int64_t sol_cap,
-                     int32_t *pre_u, double *pre_rho, int64_t pre_cap,
-                     oracle_enum_stats *out)
+int oracle_enumerate_bounds(int dd, int dim, const double *mu, const double *B, const double *bhat,
+                            const int32_t *kb, int m, int n, const int32_t *A, const int64_t *d,
+                            const int32_t *r, const oracle_enum_opts *o, const int32_t *prefix_u,
+                            uint8_t *sol, int64_t sol_cap,
+                            int32_t *pre_u, double *pre_rho, int64_t pre_cap,
+                            oracle_enum_stats *out)
 {
     if (dd < 1 || dim != n + 1) return OR_EINVAL;
+    const int64_t rmax = oracle_rmax(n, r);
+    if (rmax < 1) return OR_EINVAL;
     if (o->lanes < 1 || o->lanes > 64 || (o->lanes & (o->lanes - 1))) return OR_EINVAL;
     enum_state e;
     memset(&e, 0, sizeof e);
     e.dd = dd; e.dim = dim; e.m = m; e.n = n;
     e.mu = mu; e.B = B; e.bhat = bhat; e.kb = kb; e.A = A; e.d = d;
+    e.r = r; e.rmax = rmax;
     e.o = *o;
-    const double R = (double)dim;                   /* R = (n+1) r_max^2 */
+    const double R = (double)(dim * rmax * rmax);   /* R = (n+1) r_max^2 */
     e.eps = o->use_eps ? R * 0x1p-20 : 0.0;
     e.Rb = R + e.eps;
     e.sol = sol; e.sol_cap = sol_cap;
@@ -701,6 +743,17 @@ done:
     if (nodes_out) *nodes_out = nodes;
     free(mu); free(r); free(B); free(G); free(rows); free(u); free(best); free(a);
     return st;
+}
+
+int oracle_enumerate(int dd, int dim, const double *mu, const double *B, const double *bhat,
+                     const int32_t *kb, int m, int n, const int32_t *A, const int64_t *d,
+                     const oracle_enum_opts *o, const int32_t *prefix_u,
+                     uint8_t *sol, int64_t sol_cap,
+                     int32_t *pre_u, double *pre_rho, int64_t pre_cap,
+                     oracle_enum_stats *out)
+{
+    return oracle_enumerate_bounds(dd, dim, mu, B, bhat, kb, m, n, A, d, NULL, o, prefix_u, sol, sol_cap,
+                                   pre_u, pre_rho, pre_cap, out);
 }
 
 /* Version tag so tests can check they loaded this file's build. */

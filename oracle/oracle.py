@@ -52,6 +52,12 @@ def lib():
         L = C.CDLL(path)
         P = C.c_void_p
         L.oracle_build_lattice.argtypes = [C.c_int, C.c_int, P, P, C.c_int64, P]
+        L.oracle_build_lattice_bounds.argtypes = [C.c_int, C.c_int, P, P, P, C.c_int64, P]
+        L.oracle_rmax.argtypes = [C.c_int, P]
+        L.oracle_rmax.restype = C.c_int64
+        L.oracle_enumerate_bounds.argtypes = [C.c_int, C.c_int, P, P, P, P, C.c_int, C.c_int, P, P, P,
+                                              C.POINTER(_EnumOpts), P, P, C.c_int64, P, P, C.c_int64,
+                                              C.POINTER(_EnumStats)]
         L.oracle_lll.argtypes = [C.c_int, C.c_int, P, C.c_double, C.c_double, C.c_int64, P, P]
         L.oracle_extract.argtypes = [C.c_int, C.c_int, P, P, P]
         L.oracle_gso.argtypes = [C.c_int, C.c_int, P, P, P, P]
@@ -72,13 +78,32 @@ def _check(st: int, what: str):
         raise OracleError(f"{what}: {ERRORS.get(st, st)}")
 
 
-def build_lattice(A: np.ndarray, d: np.ndarray, N: int = 1024) -> np.ndarray:
-    """Basis vectors of Eq. (2) as rows: shape (n+1, m+n+1), int64."""
+def _bounds(r, n):
+    if r is None:
+        return None
+    r = np.ascontiguousarray(r, dtype=np.int32)
+    assert r.shape == (n,)
+    return r
+
+
+def rmax(r) -> int:
+    """lcm of the upper bounds (Sec. 2); 1 for binary problems."""
+    if r is None:
+        return 1
+    r = np.ascontiguousarray(r, dtype=np.int32)
+    return int(lib().oracle_rmax(len(r), _p(r)))
+
+
+def build_lattice(A: np.ndarray, d: np.ndarray, N: int = 1024, r=None) -> np.ndarray:
+    """Basis vectors of Eq. (2) as rows: shape (n+1, m+n+1), int64.  r: upper
+    bounds of x (None: binary)."""
     A = np.ascontiguousarray(A, dtype=np.int32)
     d = np.ascontiguousarray(d, dtype=np.int64)
     m, n = A.shape
+    rb = _bounds(r, n)
     basis = np.zeros((n + 1, m + n + 1), dtype=np.int64)
-    _check(lib().oracle_build_lattice(m, n, _p(A), _p(d), N, _p(basis)), "build_lattice")
+    _check(lib().oracle_build_lattice_bounds(m, n, _p(A), _p(d), _p(rb) if rb is not None else None, N,
+                                             _p(basis)), "build_lattice")
     return basis
 
 
@@ -177,7 +202,7 @@ def enumerate(kern: np.ndarray, g: GSO, A: np.ndarray, d: np.ndarray, *,
               hoelder: int = HOELDER_CUT, sym: bool = True, lanes: int = 32,
               use_eps: bool = True, first: bool = False,
               split_level: int = -1, sub_level: int = -1,
-              prefix: Optional[np.ndarray] = None, lds: int = -1,
+              prefix: Optional[np.ndarray] = None, lds: int = -1, r=None,
               sol_cap: int = 1 << 16, prefix_cap: int = 1 << 20) -> EnumResult:
     """Algorithm 1 over the whole tree, the top part down to ``split_level``
     (recording prefixes), or the subtree below ``prefix`` at ``sub_level``.
@@ -194,10 +219,12 @@ def enumerate(kern: np.ndarray, g: GSO, A: np.ndarray, d: np.ndarray, *,
     pre_u = np.zeros((max(pcap, 1), dd), np.int32)
     pre_rho = np.zeros(max(pcap, 1), np.float64)
     st = _EnumStats()
-    _check(lib().oracle_enumerate(dd, dim, _p(np.ascontiguousarray(g.mu)), _p(np.ascontiguousarray(g.B)),
-                                  _p(np.ascontiguousarray(g.bhat)), _p(kb), m, n, _p(A), _p(d),
-                                  C.byref(o), _p(pu), _p(sol), sol_cap, _p(pre_u), _p(pre_rho), pcap,
-                                  C.byref(st)), "enumerate")
+    rb = _bounds(r, n)
+    _check(lib().oracle_enumerate_bounds(dd, dim, _p(np.ascontiguousarray(g.mu)), _p(np.ascontiguousarray(g.B)),
+                                         _p(np.ascontiguousarray(g.bhat)), _p(kb), m, n, _p(A), _p(d),
+                                         _p(rb) if rb is not None else None,
+                                         C.byref(o), _p(pu), _p(sol), sol_cap, _p(pre_u), _p(pre_rho), pcap,
+                                         C.byref(st)), "enumerate")
     if st.nsol > sol_cap:
         raise OracleError(f"enumerate: {st.nsol} solutions exceed sol_cap={sol_cap}")
     if pcap and st.nprefix > pcap:
@@ -234,18 +261,18 @@ class Solved:
     lll_iterations: int
 
 
-def reduce(A: np.ndarray, d: np.ndarray, N: int = 1024, delta: float = 0.99):
+def reduce(A: np.ndarray, d: np.ndarray, N: int = 1024, delta: float = 0.99, r=None):
     """Alg. 1 steps 1-3: lattice of Eq. (2), LLL, extraction, Gram-Schmidt."""
     A = np.ascontiguousarray(A, dtype=np.int32)
     m = A.shape[0]
-    red = lll(build_lattice(A, d, N), delta=delta)
+    red = lll(build_lattice(A, d, N, r=r), delta=delta)
     kern = extract(red.basis, m)
     return red, kern, gso(kern)
 
 
-def solve(A: np.ndarray, d: np.ndarray, N: int = 1024, delta: float = 0.99, **kw) -> Solved:
-    red, kern, g = reduce(A, d, N, delta)
-    res = enumerate(kern, g, A, d, **kw)
+def solve(A: np.ndarray, d: np.ndarray, N: int = 1024, delta: float = 0.99, r=None, **kw) -> Solved:
+    red, kern, g = reduce(A, d, N, delta, r=r)
+    res = enumerate(kern, g, A, d, r=r, **kw)
     return Solved(red.basis, kern, g, res, red.iterations)
 
 

@@ -32,6 +32,7 @@ class Instance:
     seed: int
     D: int
     tag: str = ""
+    r: Optional[np.ndarray] = None   # int32 (n,) upper bounds 0 <= x <= r; None: binary
 
     @property
     def m(self) -> int:
@@ -116,6 +117,17 @@ def small(seed: int, m: int, n: int, D: int) -> Instance:
     return make_instance(seed, m, n, D, tag=f"small_m{m}n{n}D{D}")
 
 
+def bounded(seed: int, m: int, n: int, D: int, bounds=(1, 2, 3)) -> Instance:
+    """The general problem of Sec. 2: 0 <= x_j <= r_j with r_j drawn from
+    ``bounds``, A uniform in [0, D), a planted x uniform in the box, d = A x."""
+    rng = np.random.default_rng(seed)
+    A = rng.integers(0, D, size=(m, n)).astype(np.int32)
+    r = rng.choice(np.asarray(bounds, dtype=np.int32), size=n).astype(np.int32)
+    x = np.array([rng.integers(0, int(rj) + 1) for rj in r], dtype=np.uint8)
+    d = (A.astype(np.int64) @ x.astype(np.int64)).astype(np.int64)
+    return Instance(A=A, d=d, planted=x, seed=seed, D=D, tag=f"bounded_m{m}n{n}D{D}_{seed}", r=r)
+
+
 # --- packing for the batched C-ABI -------------------------------------------
 
 @dataclass
@@ -126,6 +138,7 @@ class Packed:
     A: np.ndarray                    # int32 (sum m_i n_i,)
     d: np.ndarray                    # int64 (sum m_i,)
     instances: List[Instance] = field(default_factory=list)
+    r: Optional[np.ndarray] = None   # int32 (sum n_i,) upper bounds, None when all binary
 
 
 def pack(instances: List[Instance]) -> Packed:
@@ -134,5 +147,9 @@ def pack(instances: List[Instance]) -> Packed:
         else np.zeros(0, np.int32)
     d = np.concatenate([x.d.reshape(-1) for x in instances]).astype(np.int64) if instances \
         else np.zeros(0, np.int64)
+    r = None
+    if any(x.r is not None for x in instances):
+        r = np.concatenate([x.r if x.r is not None else np.ones(x.n, np.int32) for x in instances]).astype(np.int32)
+        r = np.ascontiguousarray(r)
     return Packed(dims=np.ascontiguousarray(dims), A=np.ascontiguousarray(A),
-                  d=np.ascontiguousarray(d), instances=list(instances))
+                  d=np.ascontiguousarray(d), instances=list(instances), r=r)
