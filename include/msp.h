@@ -166,6 +166,20 @@ MSP_API void msp_destroy(msp_ctx *ctx);
 MSP_API msp_status msp_build_lattice(msp_ctx *ctx, int count, const int32_t *dims,
                              const int32_t *A, const int64_t *d, int mem);
 
+/* The general problem of Sec. 2: A x = d with 0 <= x_j <= r_j (bounds l
+ * are removed beforehand by x := x - l, d := d - A l).  Same as
+ * msp_build_lattice with the upper bounds
+ *   r     host int32, the r_i (n_i entries each) back to back, always host
+ *         memory; NULL: every bound is 1 (the binary problem).
+ * The lattice of Eq. (2) uses r_max = lcm(r_1 .. r_n) and c_j = r_max / r_j;
+ * the enumeration bounds become R = (n+1) r_max^2 and r_max ||w||_1 and the
+ * leaf test of Theorem 1 reads x_j = (v_j + r_max) / (2 c_j).  Limits
+ * (MSP_EINVAL otherwise): 1 <= r_j <= 255, r_max <= 1024, and the
+ * solution of an instance must fit 128 bits: sum_j bitwidth(r_j) <= 128.
+ * msp_solutions() then returns x_j in 0 .. r_j. */
+MSP_API msp_status msp_build_lattice_bounds(msp_ctx *ctx, int count, const int32_t *dims,
+                                    const int32_t *A, const int64_t *d, const int32_t *r, int mem);
+
 /* Steps a2-a3 -- Alg. 1 steps 1-3: LLL-reduce every generator (exact
  * integer basis, exact int64 Gram matrix, FP64 Gram-Schmidt), keep the
  * reduced vectors whose first m entries are zero, drop those rows and
@@ -213,7 +227,8 @@ MSP_API int msp_lanes(const msp_ctx *ctx);
 MSP_API msp_status msp_wait(msp_ctx *ctx, msp_stats *stats, msp_stats *total);
 
 /* Solutions of instance `inst` after msp_enumerate / msp_wait: writes up to
- * cap rows of n bytes (0/1), lexicographically sorted, into host memory x,
+ * cap rows of n bytes (x_j: 0/1, or 0 .. r_j with msp_build_lattice_bounds),
+ * lexicographically sorted, into host memory x,
  * and the full count into *count.  cap = 0 (x may be NULL) only queries the
  * count.  Returns MSP_ETRUNC when the count exceeds cap or the context's
  * solution capacity. */

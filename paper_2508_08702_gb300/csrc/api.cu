@@ -24,7 +24,7 @@ __global__ void prep_fixed_kernel(Pools P, int use_eps, int dimPad);
 cudaError_t launch_split(const Pools& P, const EnumCfg& cfg, int lanes, int max_depth, int64_t target,
                          int64_t* fcnt, cudaStream_t st);
 cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
-                        int Kmax, int dimPad, cudaStream_t st);
+                        int Kmax, int dimPad, bool bounded, cudaStream_t st);
 cudaError_t launch_collect(const Pools& P, int64_t* soff, unsigned long long* fill, SolRec* seg, SolRec* out,
                            cudaStream_t st);
 cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, int keep, cudaStream_t st);
@@ -70,6 +70,8 @@ struct msp_ctx {
     int64_t F = 0;
     std::vector<InstDesc> hinst;
     std::vector<InstDesc> layout;        // descriptors as msp_build_lattice wrote them
+    std::vector<int32_t> hr;             // bounds of all instances (host copy)
+    bool bounded = false;                // some instance has r_max > 1
     std::vector<msp_stats> stats;
     int last_mode = 0;
     double last_ms = 0.0;
@@ -81,7 +83,7 @@ struct msp_ctx {
     // device buffers
     Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, bq, nbq, fu, fdisc, fxsum, frho, fw, fcnt, qbase, sols, ctrl, soff,
         fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_seq, feat, prof, yout, skeys, svals, skeys2,
-        svals2, perm, theta, mlpwork, inst0, skip, bkzs;
+        svals2, perm, theta, mlpwork, inst0, skip, bkzs, rb;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cst = nullptr;          // private stream the step is captured on
@@ -189,6 +191,7 @@ void refresh_pools(msp_ctx* c) {
     P.sols = ptr<SolRec>(c->sols);
     P.sol_cap = c->o.sol_capacity;
     P.ctrl = ptr<Ctrl>(c->ctrl);
+    P.r = ptr<int32_t>(c->rb);
 }
 
 int walkers_of(const msp_ctx* c, int blocks, int threads) { return blocks * threads / c->lanes; }
@@ -356,7 +359,7 @@ void msp_destroy(msp_ctx* c) {
                   &c->bhat, &c->bq, &c->nbq, &c->fdisc, &c->fxsum, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
                   &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols, &c->don,
                   &c->don_seq, &c->feat, &c->prof, &c->yout, &c->skeys, &c->svals, &c->skeys2, &c->svals2,
-                  &c->perm, &c->theta, &c->mlpwork, &c->inst0, &c->skip, &c->bkzs};
+                  &c->perm, &c->theta, &c->mlpwork, &c->inst0, &c->skip, &c->bkzs, &c->rb};
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->cst) cudaStreamDestroy(c->cst);
@@ -369,18 +372,47 @@ void msp_destroy(msp_ctx* c) {
 
 msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const int32_t* A, const int64_t* d,
                              int mem) {
+    return msp_build_lattice_bounds(c, count, dims, A, d, nullptr, mem);
+}
+
+msp_status msp_build_lattice_bounds(msp_ctx* c, int count, const int32_t* dims, const int32_t* A,
+                                    const int64_t* d, const int32_t* r, int mem) {
     if (!c) return MSP_EINVAL;
     if (count < 1 || !dims || !A || !d || (mem != MSP_HOST && mem != MSP_DEVICE))
         return fail(c, MSP_EINVAL, "msp_build_lattice: bad arguments");
     std::vector<InstDesc> h(count);
-    int64_t nA = 0, nd = 0, nBasis = 0, nGram = 0, nMu = 0, nK = 0, nKb = 0, nT = 0;
+    int64_t nA = 0, nd = 0, nBasis = 0, nGram = 0, nMu = 0, nK = 0, nKb = 0, nT = 0, nR = 0;
     int Kmax = 0, dimMax = 0;
+    std::vector<int32_t> hr;   // bounds of all instances (ones for binary problems)
     for (int i = 0; i < count; ++i) {
         const int m = dims[2 * i], n = dims[2 * i + 1];
         if (m < 1 || m > kMaxM || n < 1 || n + 1 > kMaxDim || m > n)
             return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(i) + " has bad (m, n)");
         InstDesc& I = h[i];
         std::memset(&I, 0, sizeof I);
+        // bounds 0 <= x_j <= r_j (Sec. 2): r_max = lcm, key fields of bound_bits(r_j) bits
+        int64_t rmax = 1;
+        int keybits = 0;
+        for (int j = 0; j < n; ++j) {
+            const int32_t rj = r ? r[nR + j] : 1;
+            if (rj < 1 || rj > 255)
+                return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(i) +
+                                               ": bounds must lie in [1, 255]");
+            int64_t a = rmax, b = rj;
+            while (b) { const int64_t t = a % b; a = b; b = t; }
+            rmax = rmax / a * rj;
+            if (rmax > 1024)
+                return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(i) +
+                                               ": lcm of the bounds exceeds 1024");
+            keybits += bound_bits(rj);
+            hr.push_back(rj);
+        }
+        if (keybits > 128)
+            return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(i) +
+                                           ": more than 128 bits of x (sum of bit widths of the bounds)");
+        I.rmax = (int32_t)rmax;
+        I.offR = nR;
+        nR += n;
         I.m = m; I.n = n; I.K = n + 1; I.L = m + n + 1; I.dim = n + 1;
         I.offA = nA; nA += (int64_t)m * n;
         I.offd = nd; nd += m;
@@ -419,6 +451,7 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     ENSURE(inst0, sizeof(InstDesc) * count);
     ENSURE(cnt, sizeof(InstCounters) * count);
     ENSURE(A, sizeof(int32_t) * nA);
+    ENSURE(rb, sizeof(int32_t) * nR);
     ENSURE(d, sizeof(int64_t) * nd);
     ENSURE(basis, sizeof(int64_t) * nBasis);
     ENSURE(gram, sizeof(int64_t) * nGram);
@@ -446,6 +479,7 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     refresh_pools(c);
     const cudaMemcpyKind kind = (mem == MSP_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaError_t e = cudaMemcpyAsync(c->A.p, A, sizeof(int32_t) * nA, kind, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->rb.p, hr.data(), sizeof(int32_t) * nR, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d.p, d, sizeof(int64_t) * nd, kind, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->inst0.p, h.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->inst.p, c->inst0.p, sizeof(InstDesc) * count, cudaMemcpyDeviceToDevice, c->st);
@@ -454,6 +488,9 @@ msp_status msp_build_lattice(msp_ctx* c, int count, const int32_t* dims, const i
     if (e != cudaSuccess) return cuda_fail(c, e, "msp_build_lattice copies");
     c->hinst = h;
     c->layout = h;
+    c->hr = hr;
+    c->bounded = false;
+    for (const InstDesc& I : h) c->bounded |= I.rmax > 1;
     // a captured step stays valid for new A, d of the same layout in the same buffers
     if (c->gexec && (std::memcmp(&c->graph_P, &c->P, sizeof(Pools)) != 0 || c->graph_inst.size() != h.size() ||
                      std::memcmp(c->graph_inst.data(), h.data(), sizeof(InstDesc) * h.size()) != 0))
@@ -561,7 +598,8 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
         Pq.qperm = ptr<int64_t>(c->perm);
     }
     if (!cont) record(c, c->evs1);
-    if ((e = launch_enum(Pq, cfg, c->lanes, blocks, threads, ptr<char>(c->scratch), c->Kmax, c->dimPad, c->st)) !=
+    if ((e = launch_enum(Pq, cfg, c->lanes, blocks, threads, ptr<char>(c->scratch), c->Kmax, c->dimPad, c->bounded,
+                         c->st)) !=
         cudaSuccess)
         return cuda_fail(c, e, "enumerate");
     ++c->launches;
@@ -889,12 +927,18 @@ msp_status msp_solutions(msp_ctx* c, int inst, uint8_t* x, size_t cap, size_t* c
         if (e != cudaSuccess) return cuda_fail(c, e, "msp_solutions copy");
     }
     const int n = c->hinst[inst].n;
-    for (int64_t k = 0; k < take; ++k)
+    const int32_t* rr = c->hr.data() + c->layout[inst].offR;
+    for (int64_t k = 0; k < take; ++k) {
+        int off = 0;   // x_j: bound_bits(r_j) bits, most significant first, from key bit 127 down
         for (int j = 0; j < n; ++j) {
-            const unsigned long long w = j < 64 ? rec[k].hi : rec[k].lo;
-            const int bit = j < 64 ? 63 - j : 127 - j;
-            x[(size_t)k * n + j] = (uint8_t)((w >> bit) & 1ULL);
+            const int w = bound_bits(rr[j]);
+            const int sh = 128 - off - w;
+            unsigned long long v = sh >= 64 ? (rec[k].hi >> (sh - 64))
+                                            : ((rec[k].lo >> sh) | (sh > 0 ? rec[k].hi << (64 - sh) : 0ULL));
+            x[(size_t)k * n + j] = (uint8_t)(v & ((1ULL << w) - 1ULL));
+            off += w;
         }
+    }
     return (take < found) ? MSP_ETRUNC : MSP_OK;
 }
 

@@ -25,7 +25,8 @@ struct InstDesc {
     int32_t status;
     int32_t split_level;     // lowest level fixed by the splitter
     int32_t front_sel;       // frontier buffer holding the final prefixes
-    int32_t pad0;
+    int32_t rmax;            // lcm of the bounds 0 <= x_j <= r_j (1: binary), Sec. 2
+    int64_t offR;            // n int32         upper bounds r_j
     int64_t nprefix;         // number of prefixes (subtrees)
     int64_t offA, offd;      // A (int32, m*n), d (int64, m)
     int64_t offBasis;        // K*L int64   LLL basis, vector-major
@@ -99,7 +100,15 @@ struct Pools {
     int64_t sol_cap;
     struct Ctrl* ctrl;
     const unsigned char* skip;         // optional, per instance: 1 = no subtrees in this launch
+    const int32_t* r;                  // upper bounds of x per variable (all instances)
 };
+
+// bits of the field that holds x_j in a solution key (x_j <= r_j)
+__host__ __device__ inline int bound_bits(int r) {
+    int b = 0;
+    while (r > 0) { ++b; r >>= 1; }
+    return b;
+}
 
 // Control words of one enumeration, in device memory.
 struct Ctrl {

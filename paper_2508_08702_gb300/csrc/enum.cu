@@ -39,8 +39,13 @@ __device__ __forceinline__ int zigzag(int u1, int s, int i) {
     return (i & 1) == 0 ? u1 + s * (i >> 1) : u1 - s * ((i - 1) >> 1);
 }
 
-__device__ __forceinline__ double slack_of(int dim, int use_eps) {
-    return use_eps ? (double)dim * 0x1p-20 : 0.0;
+// R = (n+1) r_max^2 (Sec. 2) and the slack of reading R4, R 2^-20
+__device__ __forceinline__ double bound_R(const InstDesc& I) {
+    return (double)I.dim * (double)I.rmax * (double)I.rmax;
+}
+
+__device__ __forceinline__ double slack_of(double R, int use_eps) {
+    return use_eps ? R * 0x1p-20 : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -58,8 +63,10 @@ __device__ int64_t expand_parent(const Pools& P, const EnumCfg& cfg, int inst, i
     const double* muT = P.muT + I.offMuT;
     const double* Bt = P.B + I.offB;
     const double* bhat = P.bhat + I.offBhat;
-    const double eps = slack_of(dim, cfg.use_eps);
-    const double Rb = (double)dim + eps;
+    const double R = bound_R(I);
+    const double eps = slack_of(R, cfg.use_eps);
+    const double Rb = R + eps;
+    const double rmaxd = (double)I.rmax;
 
     double y = 0.0;
     bool zp = true;
@@ -104,7 +111,7 @@ __device__ int64_t expand_parent(const Pools& P, const EnumCfg& cfg, int inst, i
             for (int l = 0; l < off; ++l) sl[l] = __dadd_rn(sl[l], sl[l + off]);
         }
         bool fail = false;
-        if (cfg.hoelder != HOELDER_OFF) fail = rho > __dadd_rn(sl[0], eps);
+        if (cfg.hoelder != HOELDER_OFF) fail = rho > __dadd_rn(__dmul_rn(rmaxd, sl[0]), eps);
         if (fail && cfg.hoelder == HOELDER_CUT) {
             if (onedir) break;
             ++zi;
@@ -436,6 +443,126 @@ __device__ __noinline__ int leaf_check(const Pools& P, const EnumCfg& cfg, int i
     return ok ? 1 : 0;
 }
 
+// The same check for the general bounds of Sec. 2 (any r_max >= 1): kept
+// apart so that the binary walker's register budget is unchanged.
+template <int G, int CPL>
+__device__ __noinline__ int leaf_check_bounded(const Pools& P, const EnumCfg& cfg, int inst, const Levels& L, int u,
+                                       unsigned gmask) {
+    const InstDesc& I = P.inst[inst];
+    const int dd = I.dd, dim = I.dim, n = I.n, m = I.m;
+    const int32_t* __restrict__ kb = P.kb + I.offKb;
+    const int lg = threadIdx.x & (G - 1);
+    long long v[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        const int c = lg + G * q;
+        long long a = 0;
+        if (c < dim) {
+            a = (long long)u * kb[c];
+            for (int j = 1; j < dd; ++j) a += (long long)L.u(j) * kb[(int64_t)j * dim + c];
+        }
+        v[q] = a;
+    }
+    long long mine = 0;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) if (q == (dim - 1) / G) mine = v[q];
+    const long long last = __shfl_sync(gmask, mine, (dim - 1) % G, G);
+    // Theorem 1: last entry r_max (sign-normalised), the others in
+    // [-r_max, r_max]; x_c = (v_c + r_max) / (2 c_c), c_c = r_max / r_c
+    const long long rm = I.rmax;
+    const int32_t* __restrict__ rr = P.r + I.offR;
+    const long long sg = (cfg.sym && last == -rm) ? -1 : 1;
+    bool ok = (last * sg == rm);
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        const int c = lg + G * q;
+        const long long vc = v[q] * sg;
+        if (c < n) {
+            if (rm == 1) {
+                if (vc != 1 && vc != -1) ok = false;
+            } else {
+                const long long c2 = 2 * (rm / rr[c]);
+                if (vc > rm || vc < -rm || (vc + rm) % c2 != 0) ok = false;
+            }
+        }
+    }
+    ok = __all_sync(gmask, ok);
+    if (!ok) return 0;
+    // key: x_c in a field of bound_bits(r_c) bits, most significant first,
+    // fields in coordinate order from key bit 127 down (binary: bit 127 - c)
+    unsigned long long khi = 0, klo = 0;
+    if (rm == 1) {
+        const int gi = (threadIdx.x & 31) / G;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            const int c = lg + G * q;
+            const bool one = (c < n) && (v[q] * sg == 1);
+            unsigned bits = __ballot_sync(gmask, one) >> (gi * G);
+            if (G < 32) bits &= (1u << (G & 31)) - 1u;
+            for (int l = 0; l < G; ++l) {
+                if ((bits >> l) & 1u) {
+                    const int cc = G * q + l;   // x_cc = 1 at key bit 127 - cc
+                    if (cc < 64) khi |= 1ULL << (63 - cc);
+                    else klo |= 1ULL << (127 - cc);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            const int c = lg + G * q;
+            if (c >= n) continue;
+            int off = 0;
+            for (int j = 0; j < c; ++j) off += bound_bits(rr[j]);
+            const int w = bound_bits(rr[c]);
+            const unsigned long long x = (unsigned long long)((v[q] * sg + rm) / (2 * (rm / rr[c])));
+            const int sh = 128 - off - w;   // position of the field's lowest bit
+            if (sh >= 64) {
+                khi |= x << (sh - 64);
+            } else {
+                klo |= x << sh;
+                if (sh + w > 64) khi |= x >> (64 - sh);
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o >= 1; o >>= 1) {
+            khi |= __shfl_xor_sync(gmask, khi, o, G);
+            klo |= __shfl_xor_sync(gmask, klo, o, G);
+        }
+    }
+    // independent verification A x = d, x read back from the key
+    const int32_t* Ai = P.A + I.offA;
+    const int64_t* di = P.d + I.offd;
+    for (int i = lg; i < m; i += G) {
+        long long acc = 0;
+        int off = 0;
+        for (int c = 0; c < n; ++c) {
+            const int w = (rm == 1) ? 1 : bound_bits(rr[c]);
+            const int sh = 128 - off - w;
+            unsigned long long x = sh >= 64 ? (khi >> (sh - 64)) : ((klo >> sh) | (sh > 0 ? khi << (64 - sh) : 0ULL));
+            x &= (1ULL << w) - 1ULL;
+            acc += (long long)x * Ai[(int64_t)i * n + c];
+            off += w;
+        }
+        if (acc != di[i]) ok = false;
+    }
+    ok = __all_sync(gmask, ok);
+    if (ok && lg == 0) {
+        const unsigned long long k = atomicAdd(&P.ctrl->nsol_total, 1ULL);
+        if ((int64_t)k < P.sol_cap) {
+            SolRec r;
+            r.inst = inst; r.pad = 0; r.hi = khi; r.lo = klo;
+            P.sols[k] = r;
+        }
+        const unsigned long long prev = atomicAdd(&P.cnt[inst].nsol, 1ULL);
+        if (cfg.first && prev == 0) {   // first solution of this instance
+            P.cnt[inst].first_ns = global_time_ns() - P.ctrl->start_ns;
+            if (atomicAdd(&P.ctrl->solved, 1) + 1 >= P.ctrl->active) atomicExch(&P.ctrl->stop, 1u);
+        }
+    }
+    return ok ? 1 : 0;
+}
+
 // Canonical FP64 ||w^(t)||_1 for the node (t, x): the chain of Algorithm 1
 // rebuilt from the walk's root w^(t0+1) with the same fmas as the FP64
 // method, summed in the G-lane order.
@@ -548,7 +675,9 @@ enum : int { kFetch = 0, kWalk = 1, kDone = 2 };
 #define MSP_ENUM_MIN_BLOCKS(g) ((g) >= 8 ? 2 : 1)
 #endif
 
-template <int G, int CPL>
+// BND: the batch holds an instance with bounds beyond 0/1 (r_max > 1); the
+// binary variant keeps r_max = 1 as a compile-time constant.
+template <int G, int CPL, bool BND>
 __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     enum_kernel(Pools P, EnumCfg cfg, char* scratch, WalkerLayout WL) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -571,6 +700,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     int inst = 0, dd = 0, dim = 0, sx = 0, Sf = 0, t0 = 0, t = 0;
     int64_t gid = 0;
     long long Rbits = 0, eps_fix = 0, ehalf = 0;
+    long long rmax = 1;   // stays the constant 1 in the binary variant
     double eps = 0.0;
     const double* muT = nullptr;
     const double* Btab = nullptr;
@@ -693,9 +823,14 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 bhat = P.bhat + I.offBhat;
                 bqtab = P.bq + I.offBq;
                 nbqtab = P.nbq + I.offNbq;
-                eps = slack_of(dim, cfg.use_eps);
-                Rbits = __double_as_longlong((double)dim + eps);
-                eps_fix = (long long)dim << (Sf - 20);   // eps 2^(sx+sb), exact
+                if (BND) rmax = I.rmax;
+                {
+                    const double R = bound_R(I);
+                    eps = slack_of(R, cfg.use_eps);
+                    Rbits = __double_as_longlong(R + eps);
+                    // eps 2^(sx+sb), exact: R 2^(sx+sb-20)
+                    eps_fix = cfg.use_eps ? ((long long)dim * rmax * rmax) << (Sf - 20) : 0LL;
+                }
                 ehalf = dim;
                 zp = true;
                 if (src == 1) {
@@ -839,7 +974,8 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     if (t == 0) {
                         ++leaves;
                         if (cfg.lds < 0 || dab + (u != u1 ? 1 : 0) == cfg.lds)
-                            item_sols += leaf_check<G, CPL>(P, cfg, inst, L, u, gmask);
+                            item_sols += BND ? leaf_check_bounded<G, CPL>(P, cfg, inst, L, u, gmask)
+                                             : leaf_check<G, CPL>(P, cfg, inst, L, u, gmask);
                         act = kNext;
                     } else {
                         // ---- Hoelder test (Theorem 2) through the exact integer filter ----
@@ -856,14 +992,20 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         Ech = Epar + ((ehalf * (axq + 1)) >> 1) + nbq_t + 1;
                         bool fail = false;
                         if (cfg.hoelder != HOELDER_OFF) {
-                            const long long Lfix = (long long)lsum << kHiShift;
+                            // r_max ||w||_1 (Theorem 2 with r_max); r_max = 1 for binary problems
+                            long long Lfix = (long long)lsum << kHiShift;
+                            long long Ebase = Ech + (Ech >> 10) + (ehalf << kHiShift);
+                            if (BND && rmax != 1) { Lfix *= rmax; Ebase *= rmax; }
                             const long long M = fix_trunc(rho, Sf) - Lfix - eps_fix;
-                            const long long Etot = Ech + (Ech >> 10) + (ehalf << kHiShift) + (Lfix >> 32) + 64;
+                            const long long Etot = Ebase + (Lfix >> 32) + 64;
                             if (M > Etot) fail = true;
                             else if (M < -Etot) fail = false;
                             else {
                                 ++fallbacks;
-                                fail = rho > __dadd_rn(canonical_l1<G, CPL>(bhat, root_w, L, t0, t, x, dim, gmask), eps);
+                                fail = rho > __dadd_rn(__dmul_rn((double)rmax,
+                                                                 canonical_l1<G, CPL>(bhat, root_w, L, t0, t, x, dim,
+                                                                                      gmask)),
+                                                       eps);
                             }
                         }
                         if (fail && cfg.hoelder == HOELDER_CUT) {
@@ -1068,9 +1210,9 @@ int enum_blocks_per_sm(int lanes, int threads, int dimMax, int Kmax) {
     const int smem = enum_smem_bytes(lanes, threads, Kmax);
 #define MSP_OCC(g, c)                                                                                 \
     if (lanes == g && cpl == c) {                                                                     \
-        if (cudaFuncSetAttribute(enum_kernel<g, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) \
+        if (cudaFuncSetAttribute(enum_kernel<g, c, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) \
                 != cudaSuccess ||                                                                     \
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<g, c>, threads, smem) !=     \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<g, c, false>, threads, smem) !=     \
                 cudaSuccess) {                                                                        \
             cudaGetLastError();                                                                       \
             n = 0;                                                                                    \
@@ -1086,24 +1228,30 @@ int64_t walker_bytes(int Kmax, int dimPad) { return WalkerLayout{Kmax, dimPad}.b
 int64_t donation_slot_bytes(int Kmax, int dimPad) { return donation_stride(Kmax, dimPad); }
 
 cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
-                        int Kmax, int dimPad, cudaStream_t st) {
+                        int Kmax, int dimPad, bool bounded, cudaStream_t st) {
     WalkerLayout W{Kmax, dimPad};
     const int cpl = pick_cpl(lanes, P.dimMax);
     const int smem = enum_smem_bytes(lanes, threads, Kmax);
-#define MSP_LAUNCH(g, c)                                                                              \
-    if (lanes == g && cpl == c) {                                                                     \
+#define MSP_LAUNCH1(g, c, b)                                                                          \
+    {                                                                                                 \
         /* the shared-memory attribute is set once, outside any stream capture */                     \
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;                                     \
         cudaStreamIsCapturing(st, &cs);                                                               \
         if (cs == cudaStreamCaptureStatusNone) {                                                      \
-            cudaError_t e = cudaFuncSetAttribute(enum_kernel<g, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+            cudaError_t e = cudaFuncSetAttribute(enum_kernel<g, c, b>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
             if (e != cudaSuccess) return e;                                                           \
         }                                                                                             \
-        enum_kernel<g, c><<<blocks, threads, smem, st>>>(P, cfg, scratch, W);                         \
+        enum_kernel<g, c, b><<<blocks, threads, smem, st>>>(P, cfg, scratch, W);                      \
         return cudaGetLastError();                                                                    \
+    }
+#define MSP_LAUNCH(g, c)                                                                              \
+    if (lanes == g && cpl == c) {                                                                     \
+        if (bounded) MSP_LAUNCH1(g, c, true)                                                          \
+        else MSP_LAUNCH1(g, c, false)                                                                 \
     }
     MSP_ENUM_SHAPES(MSP_LAUNCH)
 #undef MSP_LAUNCH
+#undef MSP_LAUNCH1
     return cudaErrorInvalidValue;
 }
 

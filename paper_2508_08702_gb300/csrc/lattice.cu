@@ -22,22 +22,26 @@ namespace msp {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int64_t kEntryLimit = (int64_t)1 << 58;   // |entries| < 2^58: 128-bit dots cannot overflow
 
+// Step a1: generator of Eq. (2) with bounds 0 <= x_j <= r_j: column 0 is
+// (-N d, -r_max (n times), r_max), column j is (N a_j, 2 c_j e_j, 0).
 __global__ void __launch_bounds__(128) build_lattice_kernel(Pools P, int64_t N) {
     InstDesc& I = P.inst[blockIdx.x];
     const int m = I.m, n = I.n, K = I.K, L = I.L;
     int64_t* b = P.basis + I.offBasis;
     const int32_t* A = P.A + I.offA;
     const int64_t* d = P.d + I.offd;
+    const int32_t* r = P.r ? P.r + I.offR : nullptr;   // no bounds given: the binary problem
+    const int64_t rmax = r ? I.rmax : 1;
     bool ovf = false;
     for (int e = threadIdx.x; e < K * L; e += blockDim.x) {
         const int k = e / L, c = e % L;
         __int128 v = 0;
         if (k == 0) {
             if (c < m) v = -(__int128)N * (__int128)d[c];
-            else v = (c < m + n) ? -1 : 1;
+            else v = (c < m + n) ? -rmax : rmax;
         } else {
             if (c < m) v = (__int128)N * (__int128)A[(int64_t)c * n + (k - 1)];
-            else if (c == m + (k - 1)) v = 2;
+            else if (c == m + (k - 1)) v = 2 * (r ? rmax / r[k - 1] : 1);   // 2 c_j, c_j = r_max / r_j
         }
         if (v >= kEntryLimit || v <= -kEntryLimit) ovf = true;
         b[e] = (int64_t)v;
@@ -620,7 +624,15 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
 //   sx: |x| <= sqrt((R + eps) / B_t) on every node that passes the norm test,
 //       so trunc(x 2^sx) fits in 31 bits;
 //   sb: |bhat_tc| <= sqrt(B_t), so round(bhat 2^sb) fits in 31 bits;
-//   sx + sb <= 50 keeps |w|_1 2^(sx+sb) <= sqrt(n+1) |w|_2 2^50 inside int64.
+//   sx + sb <= 50, and with R = (n+1) r_max^2 and ||w||_1 <= (n+1) r_max + 1
+//   on passing nodes: ||w||_1 2^(sx+sb-27) < 2^31 (the walkers' int32 sum),
+//   r_max ||w||_1 2^(sx+sb) < 2^62 and (R + eps) 2^(sx+sb) < 2^62.
+__device__ __forceinline__ int ceil_log2(double v) {
+    int e;
+    const double f = frexp(v, &e);   // v = f 2^e, 0.5 <= f < 1
+    return (f == 0.5) ? e - 1 : e;
+}
+
 __global__ void __launch_bounds__(32) prep_fixed_kernel(Pools P, int use_eps, int dimPad) {
     InstDesc& I = P.inst[blockIdx.x];
     const int lane = threadIdx.x;
@@ -628,7 +640,8 @@ __global__ void __launch_bounds__(32) prep_fixed_kernel(Pools P, int use_eps, in
     const int dd = I.dd, dim = I.dim;
     const double* Bt = P.B + I.offB;
     const double* bhat = P.bhat + I.offBhat;
-    const double Rb = (double)dim + (use_eps ? (double)dim * 0x1p-20 : 0.0);
+    const double R = (double)dim * (double)I.rmax * (double)I.rmax;
+    const double Rb = R + (use_eps ? R * 0x1p-20 : 0.0);
     double xm = 0.0, bm = 0.0;
     for (int t = lane; t < dd; t += 32) xm = fmax(xm, sqrt(Rb / Bt[t]));
     for (int e = lane; e < dd * dim; e += 32) bm = fmax(bm, fabs(bhat[e]));
@@ -639,8 +652,16 @@ __global__ void __launch_bounds__(32) prep_fixed_kernel(Pools P, int use_eps, in
     int ex, eb;
     frexp(xm * 1.0001 + 1.0, &ex);   // xm < 2^ex
     frexp(bm * 1.0001 + 1.0, &eb);
-    const int sx = min(25, 30 - ex), sb = min(25, 30 - eb);
-    if (sx < 8 || sb < 8) {          // values too large for a useful filter
+    int sx = min(25, 30 - ex), sb = min(25, 30 - eb);
+    {   // caps of the sums (binary problems with n + 1 <= 128 stay at 50)
+        const double l1max = (double)dim * (double)I.rmax + 1.0;
+        int smax = 58 - ceil_log2(l1max);
+        smax = min(smax, 62 - ceil_log2(l1max * (double)I.rmax));
+        smax = min(smax, 62 - ceil_log2(Rb + 1.0));
+        if (sx + sb > smax) sb = max(8, smax - sx);
+        if (sx + sb > smax) sx = smax - sb;
+    }
+    if (sx < 8 || sb < 8 || sx + sb < 20) {   // values too large for a useful filter
         if (lane == 0) set_status(I, ST_EOVERFLOW);
         return;
     }

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(32) profile_kernel(Pools P, float* prof) {
     }
     const int sl = I.split_level;
     const double* Bt = P.B + I.offB;
-    const float R = (float)I.dim;
+    const float R = (float)I.dim * (float)I.rmax * (float)I.rmax;
     float s = 0.f;
     for (int i = lane; i < sl; i += 32) s += logf((float)Bt[i]);
     for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -64,7 +64,7 @@ __global__ void features_kernel(Pools P, const float* __restrict__ prof, float* 
         const int64_t j = gid - P.qbase[inst];
         const int64_t fo = frontier_index(P, inst, I.front_sel, j);
         const int dd = I.dd, dim = I.dim, sl = I.split_level, k = dd - sl;
-        const float R = (float)dim;
+        const float R = (float)dim * (float)I.rmax * (float)I.rmax;   // (n+1) r_max^2
         const float rho = (float)P.frho[fo];
         const double* w = P.fw + fo * P.dimPad;
         float l1 = 0.f, linf = 0.f, big = 0.f;

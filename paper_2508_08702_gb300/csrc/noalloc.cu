@@ -34,6 +34,8 @@ constexpr size_t kMuBytes = ((size_t)2 * kNoAllocMaxK * kNoAllocMaxK + kNoAllocM
 constexpr size_t kBBytes = (size_t)kNoAllocMaxK * 8;
 constexpr size_t kScratchBytes = kDescBytes + kGramBytes + kMuBytes + kBBytes;   // 395,520 bytes
 
+static_assert(sizeof(InstDesc) <= kDescBytes, "the descriptor slot of the scratch is too small");
+
 // The scratch.  In host code this name is only a host-side stand-in: the
 // device address comes from cudaGetSymbolAddress (scratch_on_current_device).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];

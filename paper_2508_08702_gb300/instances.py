@@ -148,8 +148,10 @@ def pack(instances: List[Instance]) -> Packed:
     d = np.concatenate([x.d.reshape(-1) for x in instances]).astype(np.int64) if instances \
         else np.zeros(0, np.int64)
     r = None
-    if any(x.r is not None for x in instances):
-        r = np.concatenate([x.r if x.r is not None else np.ones(x.n, np.int32) for x in instances]).astype(np.int32)
+    bounds = [getattr(x, "r", None) for x in instances]
+    if any(b is not None for b in bounds):
+        r = np.concatenate([b if b is not None else np.ones(x.n, np.int32)
+                            for b, x in zip(bounds, instances)]).astype(np.int32)
         r = np.ascontiguousarray(r)
     return Packed(dims=np.ascontiguousarray(dims), A=np.ascontiguousarray(A),
                   d=np.ascontiguousarray(d), instances=list(instances), r=r)

@@ -80,6 +80,7 @@ def load():
     L.msp_destroy.argtypes = [P]
     L.msp_destroy.restype = None
     L.msp_build_lattice.argtypes = [P, C.c_int, P, P, P, C.c_int]
+    L.msp_build_lattice_bounds.argtypes = [P, C.c_int, P, P, P, P, C.c_int]
     L.msp_reduce.argtypes = [P]
     L.msp_enumerate.argtypes = [P, C.c_int, C.c_int, C.c_double, C.POINTER(msp_stats), C.POINTER(msp_stats)]
     L.msp_run_async.argtypes = [P, C.c_int, C.c_int]
@@ -201,24 +202,28 @@ class Context:
         return int(self._L.msp_kernel_launches(self._h))
 
     # -- the C ABI -----------------------------------------------------------
-    def msp_build_lattice(self, dims: np.ndarray, A, d):
+    def msp_build_lattice(self, dims: np.ndarray, A, d, r=None):
         """dims (count, 2) int32 on the host; A, d either numpy arrays (host
-        memory) or CUDA torch tensors (device memory)."""
+        memory) or CUDA torch tensors (device memory); r: optional host int32
+        upper bounds of x, all instances back to back (None: binary)."""
         dims = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 2)
         self.dims = dims
         self.count = len(dims)
-        self._keep = (A, d)
+        rb = None if r is None else np.ascontiguousarray(r, dtype=np.int32)
+        rp = _np_ptr(rb) if rb is not None else None
+        self._keep = (A, d, rb)
         if isinstance(A, np.ndarray):
             A = np.ascontiguousarray(A, dtype=np.int32)
             d = np.ascontiguousarray(d, dtype=np.int64)
-            self._keep = (A, d)
-            st = self._L.msp_build_lattice(self._h, self.count, _np_ptr(dims), _np_ptr(A), _np_ptr(d), MSP_HOST)
+            self._keep = (A, d, rb)
+            st = self._L.msp_build_lattice_bounds(self._h, self.count, _np_ptr(dims), _np_ptr(A), _np_ptr(d), rp,
+                                                  MSP_HOST)
         else:
             import torch
             assert A.is_cuda and d.is_cuda and A.dtype == torch.int32 and d.dtype == torch.int64
             assert A.is_contiguous() and d.is_contiguous()
-            st = self._L.msp_build_lattice(self._h, self.count, _np_ptr(dims), C.c_void_p(A.data_ptr()),
-                                           C.c_void_p(d.data_ptr()), MSP_DEVICE)
+            st = self._L.msp_build_lattice_bounds(self._h, self.count, _np_ptr(dims), C.c_void_p(A.data_ptr()),
+                                                  C.c_void_p(d.data_ptr()), rp, MSP_DEVICE)
         self._check(st, "msp_build_lattice")
 
     def msp_reduce(self):
@@ -370,7 +375,7 @@ def solve(instances: Sequence, mode: int = MSP_ALL, time_cap_s: float = 0.0, all
     ctx = Context(**opts)
     if scorer is not None:
         ctx.msp_set_scorer(scorer)
-    ctx.msp_build_lattice(pk.dims, pk.A, pk.d)
+    ctx.msp_build_lattice(pk.dims, pk.A, pk.d, pk.r)
     ctx.msp_reduce()
     res = ctx.msp_enumerate(mode, order, time_cap_s, allow=allow)
     sols = [ctx.msp_solutions(i) for i in range(len(pk.dims))]
