@@ -66,6 +66,7 @@ WORKLOADS = {
     "m9_all": ("m9_n80", "all", 1200.0),    # m=9, n=80, D=100, 8 instances, 40 ones planted
     "m8_first": ("m8_n70", "first", 120.0),
     "m12_first": ("m12_n110", "first", 60.0),   # m=12, n=110, D=100, 4 instances
+    "cd8_all": ("cd8", "all", 600.0),       # Cornuejols-Dawande m=8 (nothing planted), 16 instances
 }
 
 
@@ -85,20 +86,23 @@ def extended(args):
     gen, mode, cap = WORKLOADS[args.workload]
     cap = args.cap or cap
     bkz = 10 if args.bkz is None else args.bkz
-    insts = getattr(I, gen)()
+    insts = I.cd_batch(8, 16) if gen == "cd8" else getattr(I, gen)()
     pk = I.pack(insts)
     opts = dict(bkz_beta=bkz, max_seconds=cap + 60)
     if args.lanes:
         opts["lanes"] = args.lanes
+    data = ("synthetic Cornuejols-Dawande instances (d = floor(sum a / 2), nothing planted)" if gen == "cd8"
+            else "synthetic (planted instances of the paper's shapes)")
     out = {"workload": args.workload, "instances": len(insts), "m": insts[0].m, "n": insts[0].n, "D": insts[0].D,
-           "bkz_beta": bkz, "cap_s": cap, "data": "synthetic (planted instances of the paper's shapes)",
+           "bkz_beta": bkz, "cap_s": cap, "data": data,
            "gpu": torch.cuda.get_device_name()}
     clocks = Clocks(torch.cuda.current_device())
 
     def verified(ctx, i, inst):
         xs = ctx.msp_solutions(i).astype(np.int64)
         ok = all(np.array_equal(x @ inst.A.T.astype(np.int64), inst.d) for x in xs)
-        return ok, any(np.array_equal(inst.planted, x) for x in xs), len(xs)
+        planted = inst.planted is not None and any(np.array_equal(inst.planted, x) for x in xs)
+        return ok, planted, len(xs)
 
     if mode == "all":
         ctx = M.Context(**opts)
@@ -117,7 +121,8 @@ def extended(args):
                     "status": res.status, "lanes": ctx.lanes, "phase_ms": {k: round(v, 1) for k, v in ph.items()},
                     "nodes": res.total["nodes"], "nodes_per_s": res.total["nodes"] / (ph["enumerate"] / 1e3),
                     "solutions": [c[2] for c in checks], "all_verified": all(c[0] for c in checks),
-                    "planted_found": sum(c[1] for c in checks)})
+                    "planted_found": sum(c[1] for c in checks),
+                    "proved_infeasible": sum(1 for c in checks if c[2] == 0) if res.status == M.MSP_OK else 0})
         ctx.close()
     else:
         theta = None

@@ -106,6 +106,17 @@ typedef struct {
     int bkz_beta;          /* [0] >= 2: BKZ-beta of the kernel basis after LLL (Sec. 2   */
                            /*     names LLL or BKZ for step 1); 0: LLL only              */
     int bkz_max_tours;     /* [16] BKZ tours at most (a tour without insertion ends it) */
+    int replicas;          /* [1] searches per instance, each on its own random order of */
+                           /*     the variables (Sec. 4: shuffled input bases); in       */
+                           /*     MSP_FIRST the first replica to find a solution stops  */
+                           /*     the others.  Statistics and solutions are per caller's */
+                           /*     instance; the export calls index the internal         */
+                           /*     instances (instance i, replica k: i * replicas + k).   */
+                           /*     At most 64.                                            */
+    uint64_t replica_seed; /* [0x5EED5EED5EED5EED] replica k > 0 of instance i shuffles   */
+                           /*     its columns by Fisher-Yates (j = n-1 .. 1, swap j with */
+                           /*     z mod (j+1)) fed by splitmix64 from                    */
+                           /*     replica_seed ^ (i << 32) ^ k; replica 0 is unshuffled  */
 } msp_opts;
 
 /* Per-instance results of an enumeration. */

@@ -21,6 +21,7 @@ __global__ void extract_gso_kernel(Pools P, int gso_only);
 __global__ void bkz_kernel(Pools P, BkzScratch S, int beta, double delta, int max_tours, int64_t lll_max_iter,
                            unsigned long long max_ns);
 __global__ void prep_fixed_kernel(Pools P, int use_eps, int dimPad);
+__global__ void permute_kernel(Pools P, int32_t* perm, int32_t* rperm, unsigned long long seed);
 cudaError_t launch_split(const Pools& P, const EnumCfg& cfg, int lanes, int max_depth, int64_t target,
                          int64_t* fcnt, cudaStream_t st);
 cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
@@ -72,6 +73,8 @@ struct msp_ctx {
     std::vector<InstDesc> layout;        // descriptors as msp_build_lattice wrote them
     std::vector<int32_t> hr;             // bounds of all instances (host copy)
     bool bounded = false;                // some instance has r_max > 1
+    int ucount = 0;                      // the caller's instances (count = ucount x replicas)
+    std::vector<int32_t> hperm;          // column permutation of every replica (host copy)
     std::vector<msp_stats> stats;
     int last_mode = 0;
     double last_ms = 0.0;
@@ -83,7 +86,7 @@ struct msp_ctx {
     // device buffers
     Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, bq, nbq, fu, fdisc, fxsum, frho, fw, fcnt, qbase, sols, ctrl, soff,
         fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_seq, feat, prof, yout, skeys, svals, skeys2,
-        svals2, perm, theta, mlpwork, inst0, skip, bkzs, rb;
+        svals2, perm, theta, mlpwork, inst0, skip, bkzs, rb, gsolved, gfirst, colperm;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cst = nullptr;          // private stream the step is captured on
@@ -192,6 +195,8 @@ void refresh_pools(msp_ctx* c) {
     P.sol_cap = c->o.sol_capacity;
     P.ctrl = ptr<Ctrl>(c->ctrl);
     P.r = ptr<int32_t>(c->rb);
+    P.gsolved = ptr<unsigned>(c->gsolved);
+    P.gfirst_ns = ptr<unsigned long long>(c->gfirst);
 }
 
 int walkers_of(const msp_ctx* c, int blocks, int threads) { return blocks * threads / c->lanes; }
@@ -294,6 +299,8 @@ void msp_default_opts(msp_opts* o) {
     o->first_split_target = 16384;
     o->bkz_beta = 0;
     o->bkz_max_tours = 16;
+    o->replicas = 1;
+    o->replica_seed = 0x5EED5EED5EED5EEDULL;
 }
 
 const char* msp_status_string(int s) {
@@ -329,7 +336,8 @@ msp_status msp_create(msp_ctx** out, const msp_opts* opts, void* stream) {
         o.split_depth < 0 || o.warps_per_block < 1 || o.warps_per_block > 8 || o.sol_capacity < 1 ||
         o.lll_max_iter < 1 || !(o.max_seconds > 0.0) || o.donation_capacity < 0 || o.lds_budget < -1 ||
         o.lds_budget > 127 || o.lds_max < 0 || o.lds_max > 127 || o.first_split_target < 0 ||
-        o.bkz_beta < 0 || o.bkz_beta == 1 || o.bkz_beta > 128 || o.bkz_max_tours < 1) {
+        o.bkz_beta < 0 || o.bkz_beta == 1 || o.bkz_beta > 128 || o.bkz_max_tours < 1 || o.replicas < 1 ||
+        o.replicas > 64) {
         delete c;
         return MSP_EINVAL;
     }
@@ -359,7 +367,8 @@ void msp_destroy(msp_ctx* c) {
                   &c->bhat, &c->bq, &c->nbq, &c->fdisc, &c->fxsum, &c->fu, &c->frho, &c->fw, &c->fcnt, &c->qbase, &c->sols, &c->ctrl, &c->soff,
                   &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols, &c->don,
                   &c->don_seq, &c->feat, &c->prof, &c->yout, &c->skeys, &c->svals, &c->skeys2, &c->svals2,
-                  &c->perm, &c->theta, &c->mlpwork, &c->inst0, &c->skip, &c->bkzs, &c->rb};
+                  &c->perm, &c->theta, &c->mlpwork, &c->inst0, &c->skip, &c->bkzs, &c->rb, &c->gsolved,
+                  &c->gfirst, &c->colperm};
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->cst) cudaStreamDestroy(c->cst);
@@ -380,51 +389,67 @@ msp_status msp_build_lattice_bounds(msp_ctx* c, int count, const int32_t* dims, 
     if (!c) return MSP_EINVAL;
     if (count < 1 || !dims || !A || !d || (mem != MSP_HOST && mem != MSP_DEVICE))
         return fail(c, MSP_EINVAL, "msp_build_lattice: bad arguments");
-    std::vector<InstDesc> h(count);
+    const int R = c->o.replicas;   // searches per caller's instance (shuffled column orders)
+    const int total = count * R;
+    std::vector<InstDesc> h(total);
     int64_t nA = 0, nd = 0, nBasis = 0, nGram = 0, nMu = 0, nK = 0, nKb = 0, nT = 0, nR = 0;
+    int64_t uA = 0, ud = 0, uR = 0;   // offsets in the caller's arrays
     int Kmax = 0, dimMax = 0;
-    std::vector<int32_t> hr;   // bounds of all instances (ones for binary problems)
-    for (int i = 0; i < count; ++i) {
-        const int m = dims[2 * i], n = dims[2 * i + 1];
+    std::vector<int32_t> hr;   // bounds of all internal instances (ones for binary problems)
+    std::vector<int64_t> srcA(total), srcd(total);
+    for (int g = 0; g < count; ++g) {
+        const int m = dims[2 * g], n = dims[2 * g + 1];
         if (m < 1 || m > kMaxM || n < 1 || n + 1 > kMaxDim || m > n)
-            return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(i) + " has bad (m, n)");
-        InstDesc& I = h[i];
-        std::memset(&I, 0, sizeof I);
+            return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(g) + " has bad (m, n)");
         // bounds 0 <= x_j <= r_j (Sec. 2): r_max = lcm, key fields of bound_bits(r_j) bits
         int64_t rmax = 1;
         int keybits = 0;
         for (int j = 0; j < n; ++j) {
-            const int32_t rj = r ? r[nR + j] : 1;
+            const int32_t rj = r ? r[uR + j] : 1;
             if (rj < 1 || rj > 255)
-                return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(i) +
+                return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(g) +
                                                ": bounds must lie in [1, 255]");
             int64_t a = rmax, b = rj;
             while (b) { const int64_t t = a % b; a = b; b = t; }
             rmax = rmax / a * rj;
             if (rmax > 1024)
-                return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(i) +
+                return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(g) +
                                                ": lcm of the bounds exceeds 1024");
             keybits += bound_bits(rj);
-            hr.push_back(rj);
         }
         if (keybits > 128)
-            return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(i) +
+            return fail(c, MSP_EINVAL, "msp_build_lattice: instance " + std::to_string(g) +
                                            ": more than 128 bits of x (sum of bit widths of the bounds)");
-        I.rmax = (int32_t)rmax;
-        I.offR = nR;
-        nR += n;
-        I.m = m; I.n = n; I.K = n + 1; I.L = m + n + 1; I.dim = n + 1;
-        I.offA = nA; nA += (int64_t)m * n;
-        I.offd = nd; nd += m;
-        I.offBasis = nBasis; nBasis += (int64_t)I.K * I.L;
-        I.offGram = nGram; nGram += (int64_t)I.K * I.K;
-        I.offMu = nMu; nMu += (int64_t)2 * I.K * I.K + I.K;
-        I.offBl = nK; I.offB = nK; nK += I.K;
-        I.offKb = nKb; I.offBhat = nKb; nKb += (int64_t)I.K * I.dim;
-        I.offMuT = nT; nT += (int64_t)I.K * I.K;
-        Kmax = std::max(Kmax, I.K);
-        dimMax = std::max(dimMax, I.dim);
+        for (int k = 0; k < R; ++k) {
+            const int i = g * R + k;
+            InstDesc& I = h[i];
+            std::memset(&I, 0, sizeof I);
+            I.group = g;
+            I.replica = k;
+            I.rmax = (int32_t)rmax;
+            I.offR = nR;
+            for (int j = 0; j < n; ++j) hr.push_back(r ? r[uR + j] : 1);
+            nR += n;
+            I.m = m; I.n = n; I.K = n + 1; I.L = m + n + 1; I.dim = n + 1;
+            I.offA = nA; nA += (int64_t)m * n;
+            I.offd = nd; nd += m;
+            srcA[i] = uA;
+            srcd[i] = ud;
+            I.offBasis = nBasis; nBasis += (int64_t)I.K * I.L;
+            I.offGram = nGram; nGram += (int64_t)I.K * I.K;
+            I.offMu = nMu; nMu += (int64_t)2 * I.K * I.K + I.K;
+            I.offBl = nK; I.offB = nK; nK += I.K;
+            I.offKb = nKb; I.offBhat = nKb; nKb += (int64_t)I.K * I.dim;
+            I.offMuT = nT; nT += (int64_t)I.K * I.K;
+            Kmax = std::max(Kmax, I.K);
+            dimMax = std::max(dimMax, I.dim);
+        }
+        uA += (int64_t)m * n;
+        ud += m;
+        uR += n;
     }
+    c->ucount = count;
+    count = total;   // from here on: the internal instances
     c->count = count;
     c->Kmax = Kmax;
     c->dimMax = dimMax;
@@ -474,18 +499,42 @@ msp_status msp_build_lattice_bounds(msp_ctx* c, int count, const int32_t* dims, 
     ENSURE(sout, sizeof(SolRec) * (size_t)c->o.sol_capacity);
     ENSURE(scratch, (size_t)walkers * walker_bytes(Kmax, c->dimPad));
     ENSURE(prof, sizeof(float) * 17 * (size_t)count);
+    ENSURE(colperm, sizeof(int32_t) * nR);
+    ENSURE(gsolved, sizeof(unsigned) * c->ucount);
+    ENSURE(gfirst, sizeof(unsigned long long) * c->ucount);
 #undef ENSURE
     if ((s = size_frontier(c, F)) != MSP_OK) return s;
     refresh_pools(c);
     const cudaMemcpyKind kind = (mem == MSP_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    cudaError_t e = cudaMemcpyAsync(c->A.p, A, sizeof(int32_t) * nA, kind, c->st);
+    cudaError_t e = cudaSuccess;
+    if (R == 1) {
+        e = cudaMemcpyAsync(c->A.p, A, sizeof(int32_t) * nA, kind, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d.p, d, sizeof(int64_t) * nd, kind, c->st);
+    } else {   // every replica starts from the caller's A and d
+        for (int i = 0; i < count && e == cudaSuccess; ++i) {
+            const InstDesc& I = h[i];
+            e = cudaMemcpyAsync(ptr<int32_t>(c->A) + I.offA, A + srcA[i], sizeof(int32_t) * I.m * I.n, kind, c->st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(ptr<int64_t>(c->d) + I.offd, d + srcd[i], sizeof(int64_t) * I.m, kind, c->st);
+        }
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->rb.p, hr.data(), sizeof(int32_t) * nR, cudaMemcpyHostToDevice, c->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d.p, d, sizeof(int64_t) * nd, kind, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->inst0.p, h.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->inst.p, c->inst0.p, sizeof(InstDesc) * count, cudaMemcpyDeviceToDevice, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);   // h is a host temporary
     if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt.p, 0, sizeof(InstCounters) * count, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "msp_build_lattice copies");
+    c->hperm.assign(nR, 0);
+    if (R > 1) {   // shuffled column orders of the replicas (and their bounds)
+        permute_kernel<<<count, 128, 0, c->st>>>(c->P, ptr<int32_t>(c->colperm), ptr<int32_t>(c->rb),
+                                                c->o.replica_seed);
+        ++c->launches;
+        if ((s = check_launch(c, "permute_kernel")) != MSP_OK) return s;
+        e = cudaMemcpyAsync(c->hperm.data(), c->colperm.p, sizeof(int32_t) * nR, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hr.data(), c->rb.p, sizeof(int32_t) * nR, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "permute");
+    }
     c->hinst = h;
     c->layout = h;
     c->hr = hr;
@@ -550,6 +599,8 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
     if ((s = fit_frontier(c, mode, walkers)) != MSP_OK) return s;
     const int64_t target = std::min<int64_t>(split_target_of(c, mode, walkers), c->F);
     cudaError_t e = cont ? cudaSuccess : cudaMemsetAsync(c->cnt.p, 0, sizeof(InstCounters) * c->count, c->st);
+    if (e == cudaSuccess && !cont) e = cudaMemsetAsync(c->gsolved.p, 0, sizeof(unsigned) * c->ucount, c->st);
+    if (e == cudaSuccess && !cont) e = cudaMemsetAsync(c->gfirst.p, 0, sizeof(unsigned long long) * c->ucount, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->plog_nodes.p, 0, c->plog_nodes.bytes, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->plog_sols.p, 0, c->plog_sols.bytes, c->st);
     if (e == cudaSuccess && c->o.donation_capacity > 0) e = launch_ring_init(ptr<unsigned long long>(c->don_seq), c->o.donation_capacity, c->st);
@@ -642,12 +693,15 @@ static msp_status run_lds(msp_ctx* c, int mode, double time_cap_s) {
         if (e == cudaSuccess) e = cudaMemcpy(h.data(), c->inst.p, sizeof(InstDesc) * n, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) e = cudaMemcpy(&ctl, c->ctrl.p, sizeof(Ctrl), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(c, e, "lds iteration");
+        std::vector<unsigned> gs(c->ucount, 0);
+        e = cudaMemcpy(gs.data(), c->gsolved.p, sizeof(unsigned) * c->ucount, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lds iteration");
         bool all_done = true;
         for (int i = 0; i < n; ++i) {
             if (skip[i]) continue;
             const unsigned long long cuts = cn[i].lds_cuts - cuts_seen[i];
             cuts_seen[i] = cn[i].lds_cuts;
-            const bool finished = h[i].status != ST_OK || (mode == MSP_FIRST && cn[i].nsol > 0) || cuts == 0;
+            const bool finished = h[i].status != ST_OK || (mode == MSP_FIRST && gs[h[i].group]) || cuts == 0;
             if (finished) {
                 skip[i] = 1;
                 c->lds_done[i] = k;
@@ -741,6 +795,49 @@ msp_status msp_graph_launch(msp_ctx* c) {
     return MSP_OK;
 }
 
+// The stored solutions of internal instance i, decoded (x_j in a field of
+// bound_bits(r_j) bits, most significant first, from key bit 127 down) and
+// put back in the caller's column order (replica k > 0 permuted them).
+static msp_status decode_instance(msp_ctx* c, int i, std::vector<std::vector<uint8_t>>& out) {
+    const int64_t lo = c->soff_h[i], have = c->soff_h[i + 1] - lo;
+    std::vector<SolRec> rec((size_t)std::max<int64_t>(have, 0));
+    if (have > 0) {
+        cudaError_t e = cudaMemcpy(rec.data(), ptr<SolRec>(c->sout) + lo, sizeof(SolRec) * have, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "msp_solutions copy");
+    }
+    const InstDesc& I = c->layout[i];
+    const int n = I.n;
+    const int32_t* rr = c->hr.data() + I.offR;
+    const int32_t* pi = c->hperm.data() + I.offR;
+    const bool permuted = c->ucount != c->count && I.replica > 0;
+    for (const SolRec& q : rec) {
+        std::vector<uint8_t> x(n);
+        int off = 0;
+        for (int j = 0; j < n; ++j) {
+            const int w = bound_bits(rr[j]);
+            const int sh = 128 - off - w;
+            const unsigned long long v =
+                sh >= 64 ? (q.hi >> (sh - 64)) : ((q.lo >> sh) | (sh > 0 ? q.hi << (64 - sh) : 0ULL));
+            x[permuted ? pi[j] : j] = (uint8_t)(v & ((1ULL << w) - 1ULL));
+            off += w;
+        }
+        out.push_back(std::move(x));
+    }
+    return MSP_OK;
+}
+
+// All replicas' solutions of the caller's instance g, sorted and distinct.
+static msp_status group_solutions(msp_ctx* c, int g, std::vector<std::vector<uint8_t>>& out) {
+    const int R = c->count / c->ucount;
+    for (int k = 0; k < R; ++k) {
+        msp_status s = decode_instance(c, g * R + k, out);
+        if (s != MSP_OK) return s;
+    }
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+    return MSP_OK;
+}
+
 msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {
     if (!c) return MSP_EINVAL;
     if (c->state < 3) return fail(c, MSP_ESTATE, "msp_wait before an enumeration");
@@ -809,7 +906,44 @@ msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {
     tot.ms = ms;
     tot.donations = (int64_t)ctl.donations;
     tot.walker_util = ctl.life_cycles ? (double)ctl.walk_cycles / (double)ctl.life_cycles : 0.0;
-    if (stats) std::memcpy(stats, c->stats.data(), sizeof(msp_stats) * c->count);
+    if (c->ucount != c->count) {   // replicas: one record per caller's instance
+        c->sout_valid = false;
+        std::vector<unsigned> gs(c->ucount, 0);
+        std::vector<unsigned long long> gf(c->ucount, 0);
+        e = cudaMemcpy(gs.data(), c->gsolved.p, sizeof(unsigned) * c->ucount, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(gf.data(), c->gfirst.p, sizeof(unsigned long long) * c->ucount,
+                                             cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "reading group results");
+        const int R = c->count / c->ucount;
+        std::vector<msp_stats> u(c->ucount, msp_stats{});
+        tot.solutions = 0;
+        for (int g = 0; g < c->ucount; ++g) {
+            msp_stats& U = u[g];
+            U = c->stats[(size_t)g * R];   // sizes, split level, rank: replica 0
+            U.status = MSP_OK;
+            U.lds_budget = -1;
+            for (int k = 0; k < R; ++k) {
+                const msp_stats& S = c->stats[(size_t)g * R + k];
+                if (k > 0) {
+                    U.nodes += S.nodes; U.passed += S.passed; U.leaves += S.leaves; U.prefixes += S.prefixes;
+                    U.lll_iterations += S.lll_iterations; U.lll_swaps += S.lll_swaps;
+                    U.bkz_tours += S.bkz_tours; U.bkz_inserts += S.bkz_inserts; U.bkz_nodes += S.bkz_nodes;
+                    U.split_nodes += S.split_nodes; U.split_passed += S.split_passed;
+                    U.center_fma += S.center_fma; U.fallbacks += S.fallbacks;
+                }
+                if (S.status != MSP_OK && U.status == MSP_OK) U.status = S.status;
+                U.lds_budget = std::max(U.lds_budget, S.lds_budget);
+            }
+            U.first_ms = (c->last_mode == MSP_FIRST && gs[g]) ? (double)gf[g] * 1e-6 : -1.0;
+            std::vector<std::vector<uint8_t>> xs;
+            msp_status sg = group_solutions(c, g, xs);
+            if (sg != MSP_OK) return sg;
+            U.solutions = (int64_t)xs.size();
+            tot.solutions += U.solutions;
+        }
+        c->stats = u;
+    }
+    if (stats) std::memcpy(stats, c->stats.data(), sizeof(msp_stats) * c->stats.size());
     if (total) *total = tot;
     return first_bad;
 }
@@ -913,11 +1047,19 @@ msp_status msp_phase_ms(msp_ctx* c, double* out) {
 msp_status msp_solutions(msp_ctx* c, int inst, uint8_t* x, size_t cap, size_t* count) {
     if (!c || !count) return MSP_EINVAL;
     if (c->state < 3 || c->stats.empty()) return fail(c, MSP_ESTATE, "msp_solutions before msp_wait");
-    if (inst < 0 || inst >= c->count) return fail(c, MSP_EINVAL, "instance index out of range");
+    if (inst < 0 || inst >= (int)c->stats.size()) return fail(c, MSP_EINVAL, "instance index out of range");
     const int64_t found = c->stats[inst].solutions;
     *count = (size_t)found;
     if (cap == 0) return MSP_OK;
     if (!x) return MSP_EINVAL;
+    if (c->ucount != c->count) {   // replicas: the union of the replicas' solutions, caller's order
+        std::vector<std::vector<uint8_t>> xs;
+        msp_status s = group_solutions(c, inst, xs);
+        if (s != MSP_OK) return s;
+        const size_t take = std::min(xs.size(), cap);
+        for (size_t k = 0; k < take; ++k) std::memcpy(x + k * xs[k].size(), xs[k].data(), xs[k].size());
+        return (take < (size_t)found) ? MSP_ETRUNC : MSP_OK;
+    }
     const int64_t lo = c->soff_h[inst];
     const int64_t have = c->soff_h[inst + 1] - lo;   // stored records of this instance
     const int64_t take = std::min<int64_t>(have, (int64_t)cap);

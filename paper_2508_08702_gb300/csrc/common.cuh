@@ -26,7 +26,8 @@ struct InstDesc {
     int32_t split_level;     // lowest level fixed by the splitter
     int32_t front_sel;       // frontier buffer holding the final prefixes
     int32_t rmax;            // lcm of the bounds 0 <= x_j <= r_j (1: binary), Sec. 2
-    int64_t offR;            // n int32         upper bounds r_j
+    int64_t offR;            // n int32         upper bounds r_j; also the column permutation
+    int32_t group, replica;  // the caller's instance and the replica of it (shuffled columns)
     int64_t nprefix;         // number of prefixes (subtrees)
     int64_t offA, offd;      // A (int32, m*n), d (int64, m)
     int64_t offBasis;        // K*L int64   LLL basis, vector-major
@@ -101,6 +102,8 @@ struct Pools {
     struct Ctrl* ctrl;
     const unsigned char* skip;         // optional, per instance: 1 = no subtrees in this launch
     const int32_t* r;                  // upper bounds of x per variable (all instances)
+    unsigned* gsolved;                 // per group (caller's instance): a replica found a solution
+    unsigned long long* gfirst_ns;     // per group: time of that first solution
 };
 
 // bits of the field that holds x_j in a solution key (x_j <= r_j)

@@ -259,12 +259,12 @@ __global__ void start_kernel(Ctrl* c, unsigned long long cap_ns, int keep) {
 // exclusive prefix sums of the per-instance prefix counts (one thread)
 __global__ void queue_kernel(Pools P) {
     int64_t run = 0;
-    int active = 0;
+    int active = 0, last = -1;   // groups with work (a group's replicas are contiguous)
     for (int i = 0; i < P.count; ++i) {
         P.qbase[i] = run;
         const int64_t k = (P.inst[i].status == ST_OK) ? P.inst[i].nprefix : 0;
         run += k;
-        active += k > 0;
+        if (k > 0 && P.inst[i].group != last) { ++active; last = P.inst[i].group; }
     }
     P.ctrl->active = active;
     P.qbase[P.count] = run;
@@ -435,9 +435,13 @@ __device__ __noinline__ int leaf_check(const Pools& P, const EnumCfg& cfg, int i
             P.sols[k] = r;
         }
         const unsigned long long prev = atomicAdd(&P.cnt[inst].nsol, 1ULL);
-        if (cfg.first && prev == 0) {   // first solution of this instance
-            P.cnt[inst].first_ns = global_time_ns() - P.ctrl->start_ns;
-            if (atomicAdd(&P.ctrl->solved, 1) + 1 >= P.ctrl->active) atomicExch(&P.ctrl->stop, 1u);
+        if (cfg.first) {
+            const unsigned long long now = global_time_ns() - P.ctrl->start_ns;
+            if (prev == 0) P.cnt[inst].first_ns = now;   // first solution of this replica
+            if (atomicCAS(&P.gsolved[I.group], 0u, 1u) == 0u) {   // ... and of its group
+                P.gfirst_ns[I.group] = now;
+                if (atomicAdd(&P.ctrl->solved, 1) + 1 >= P.ctrl->active) atomicExch(&P.ctrl->stop, 1u);
+            }
         }
     }
     return ok ? 1 : 0;
@@ -555,9 +559,13 @@ __device__ __noinline__ int leaf_check_bounded(const Pools& P, const EnumCfg& cf
             P.sols[k] = r;
         }
         const unsigned long long prev = atomicAdd(&P.cnt[inst].nsol, 1ULL);
-        if (cfg.first && prev == 0) {   // first solution of this instance
-            P.cnt[inst].first_ns = global_time_ns() - P.ctrl->start_ns;
-            if (atomicAdd(&P.ctrl->solved, 1) + 1 >= P.ctrl->active) atomicExch(&P.ctrl->stop, 1u);
+        if (cfg.first) {
+            const unsigned long long now = global_time_ns() - P.ctrl->start_ns;
+            if (prev == 0) P.cnt[inst].first_ns = now;   // first solution of this replica
+            if (atomicCAS(&P.gsolved[I.group], 0u, 1u) == 0u) {   // ... and of its group
+                P.gfirst_ns[I.group] = now;
+                if (atomicAdd(&P.ctrl->solved, 1) + 1 >= P.ctrl->active) atomicExch(&P.ctrl->stop, 1u);
+            }
         }
     }
     return ok ? 1 : 0;
@@ -710,6 +718,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     double y = 0.0, rhoP = 0.0, Bt = 0.0;
     int u = 0, u1 = 0, s = 1, zi = 1, dir = 0, act = kEval;
     int dab = 0;                       // discrepancies on the path above level t
+    int grp = 0;                       // the walk's group (caller's instance)
     bool onedir = false, zp = true;
     long long Epar = 0, nbq_t = 0;
     long long W[CPL], T[CPL];
@@ -798,7 +807,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     gid = hd->gid;
                 }
                 int skip = 0;
-                if (cfg.first && lg == 0) skip = *(volatile unsigned long long*)&P.cnt[inst].nsol != 0;
+                if (cfg.first && lg == 0) skip = *(volatile unsigned*)&P.gsolved[P.inst[inst].group] != 0;
                 skip = __shfl_sync(gmask, skip, 0, G);
                 if (skip) {   // instance already solved: drop the subtree
                     if (lg == 0) {
@@ -816,6 +825,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 const InstDesc& I = P.inst[inst];
                 dd = I.dd;
                 dim = I.dim;
+                grp = I.group;
                 sx = I.sx;
                 Sf = I.sx + I.sb;
                 muT = P.muT + I.offMuT;
@@ -947,7 +957,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     }
                 }
                 int solved = 0;
-                if (cfg.first && lg == 0) solved = *(volatile unsigned long long*)&P.cnt[inst].nsol != 0;
+                if (cfg.first && lg == 0) solved = *(volatile unsigned*)&P.gsolved[grp] != 0;
                 if (__shfl_sync(gmask, st, 0, G)) abort = true;
                 else if (__shfl_sync(gmask, solved, 0, G)) { abort = true; quiet = true; }
                 else if (__shfl_sync(gmask, want, 0, G))

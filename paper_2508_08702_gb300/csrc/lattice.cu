@@ -49,6 +49,56 @@ __global__ void __launch_bounds__(128) build_lattice_kernel(Pools P, int64_t N) 
     if (ovf) set_status(I, ST_EOVERFLOW);
 }
 
+// ---------------------------------------------------------------------------
+// Replicas (Sec. 4: the input order shuffled at random, one search per
+// order; the first to find a solution answers the instance).  Replica k > 0
+// of an instance permutes its variables by Fisher-Yates, j = n-1 .. 1 swapping
+// position j with position z mod (j+1), z the successive outputs of
+// splitmix64 (Steele, Lea and Flood) started at seed ^ (group << 32) ^ k.
+// perm[j] = the caller's column that becomes column j; A's columns and the
+// bounds are permuted in place.  Replica 0 keeps the caller's order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64_next(unsigned long long& state) {
+    unsigned long long z = (state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__global__ void __launch_bounds__(128) permute_kernel(Pools P, int32_t* perm, int32_t* rperm,
+                                                      unsigned long long seed) {
+    InstDesc& I = P.inst[blockIdx.x];
+    const int m = I.m, n = I.n;
+    int32_t* pi = perm + I.offR;
+    __shared__ int32_t col[128];
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < n; ++j) col[j] = j;
+        if (I.replica > 0) {
+            unsigned long long st = seed ^ ((unsigned long long)I.group << 32) ^ (unsigned long long)I.replica;
+            for (int j = n - 1; j >= 1; --j) {
+                const int k = (int)(splitmix64_next(st) % (unsigned long long)(j + 1));
+                const int t = col[j]; col[j] = col[k]; col[k] = t;
+            }
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) pi[j] = col[j];
+    if (I.replica == 0) return;
+    // rows of A and the bounds, gathered through the permutation
+    int32_t* A = const_cast<int32_t*>(P.A) + I.offA;
+    int32_t* r = rperm + I.offR;
+    __shared__ int32_t row[128];
+    for (int i = 0; i < m; ++i) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = A[(int64_t)i * n + col[j]];
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) A[(int64_t)i * n + j] = row[j];
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = r[col[j]];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) r[j] = row[j];
+}
+
 __device__ __forceinline__ int64_t dot_exact(const int64_t* __restrict__ a, const int64_t* __restrict__ b,
                                              int L, bool& ovf) {
     __int128 s = 0;

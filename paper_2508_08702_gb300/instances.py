@@ -28,7 +28,7 @@ class Instance:
 
     A: np.ndarray            # int32, shape (m, n), row-major
     d: np.ndarray            # int64, shape (m,)
-    planted: np.ndarray      # uint8, shape (n,), one known solution
+    planted: Optional[np.ndarray]   # uint8, shape (n,), one known solution (None: none planted)
     seed: int
     D: int
     tag: str = ""
@@ -126,6 +126,23 @@ def bounded(seed: int, m: int, n: int, D: int, bounds=(1, 2, 3)) -> Instance:
     x = np.array([rng.integers(0, int(rj) + 1) for rj in r], dtype=np.uint8)
     d = (A.astype(np.int64) @ x.astype(np.int64)).astype(np.int64)
     return Instance(A=A, d=d, planted=x, seed=seed, D=D, tag=f"bounded_m{m}n{n}D{D}_{seed}", r=r)
+
+
+def cornuejols_dawande(seed: int, m: int) -> Instance:
+    """The original market split instances (Sec. 1): n = 10(m-1), a_ij
+    uniform in [0, 100), d_i = floor(sum_j a_ij / 2).  Nothing is planted, so
+    feasibility is not known in advance: at m = 3..6 about a third of them
+    have no solution, and answering those takes an exhaustive search."""
+    rng = np.random.default_rng(seed)
+    n = 10 * (m - 1)
+    A = rng.integers(0, 100, size=(m, n)).astype(np.int32)
+    d = (A.astype(np.int64).sum(axis=1) // 2).astype(np.int64)
+    return Instance(A=A, d=d, planted=None, seed=seed, D=100, tag=f"cd_m{m}_{seed}")
+
+
+def cd_batch(m: int, count: int, first_seed: int = 9000) -> List[Instance]:
+    """Cornuejols-Dawande instances of one m, seeds first_seed + m * 100 + i."""
+    return [cornuejols_dawande(first_seed + m * 100 + i, m) for i in range(count)]
 
 
 # --- packing for the batched C-ABI -------------------------------------------
