@@ -712,19 +712,17 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     double eps = 0.0;
     const double* muT = nullptr;
     const double* Btab = nullptr;
-    const double* bhat = nullptr;
     const int32_t* bqtab = nullptr;
     const int64_t* nbqtab = nullptr;
     double y = 0.0, rhoP = 0.0, Bt = 0.0;
     int u = 0, u1 = 0, s = 1, zi = 1, dir = 0, act = kEval;
     int dab = 0;                       // discrepancies on the path above level t
-    int grp = 0;                       // the walk's group (caller's instance)
     bool onedir = false, zp = true;
     long long Epar = 0, nbq_t = 0;
-    long long W[CPL], T[CPL];
+    long long W[CPL];
     int bq[CPL];
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) { W[q] = 0; T[q] = 0; bq[q] = 0; }
+    for (int q = 0; q < CPL; ++q) { W[q] = 0; bq[q] = 0; }
     unsigned long long nodes = 0, passed = 0, cfma = 0;
     unsigned leaves = 0, fallbacks = 0, cuts = 0;
     int item_sols = 0;
@@ -825,12 +823,10 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 const InstDesc& I = P.inst[inst];
                 dd = I.dd;
                 dim = I.dim;
-                grp = I.group;
                 sx = I.sx;
                 Sf = I.sx + I.sb;
                 muT = P.muT + I.offMuT;
                 Btab = P.B + I.offB;
-                bhat = P.bhat + I.offBhat;
                 bqtab = P.bq + I.offBq;
                 nbqtab = P.nbq + I.offNbq;
                 if (BND) rmax = I.rmax;
@@ -957,11 +953,11 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     }
                 }
                 int solved = 0;
-                if (cfg.first && lg == 0) solved = *(volatile unsigned*)&P.gsolved[grp] != 0;
+                if (cfg.first && lg == 0) solved = *(volatile unsigned*)&P.gsolved[P.inst[inst].group] != 0;
                 if (__shfl_sync(gmask, st, 0, G)) abort = true;
                 else if (__shfl_sync(gmask, solved, 0, G)) { abort = true; quiet = true; }
                 else if (__shfl_sync(gmask, want, 0, G))
-                    donate<G>(P, inst, gid, L, root_w, bhat, t0, t, dd, dim, Kmax, cfg.lds, gmask);
+                    donate<G>(P, inst, gid, L, root_w, P.bhat + P.inst[inst].offBhat, t0, t, dd, dim, Kmax, cfg.lds, gmask);
             }
             if (u >= kUMax || u <= -kUMax) {
                 if (!abort && lg == 0) set_status(P.inst[inst], ST_EOVERFLOW);
@@ -993,8 +989,8 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         int lsum = 0;
 #pragma unroll
                         for (int q = 0; q < CPL; ++q) {
-                            T[q] = W[q] + (long long)xq * (long long)bq[q];
-                            lsum += abs((int)(T[q] >> kHiShift));
+                            const long long Tq = W[q] + (long long)xq * (long long)bq[q];
+                            lsum += abs((int)(Tq >> kHiShift));
                         }
 #pragma unroll
                         for (int off = G / 2; off >= 1; off >>= 1) lsum += __shfl_xor_sync(gmask, lsum, off, G);
@@ -1013,7 +1009,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                             else {
                                 ++fallbacks;
                                 fail = rho > __dadd_rn(__dmul_rn((double)rmax,
-                                                                 canonical_l1<G, CPL>(bhat, root_w, L, t0, t, x, dim,
+                                                                 canonical_l1<G, CPL>(P.bhat + P.inst[inst].offBhat, root_w, L, t0, t, x, dim,
                                                                                       gmask)),
                                                        eps);
                             }
@@ -1050,7 +1046,15 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     }
                     dab += (u != u1) ? 1 : 0;
 #pragma unroll
-                    for (int q = 0; q < CPL; ++q) W[q] = T[q];
+                    {
+                        // the child's W = W + xq Bq, recomputed instead of keeping the
+                        // candidate vector live across the node (registers); the opaque copy
+                        // of xq keeps the compiler from reusing the earlier products
+                        int xo;
+                        asm volatile("mov.b32 %0, %1;" : "=r"(xo) : "r"(xq));
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) W[q] += (long long)xo * (long long)bq[q];
+                    }
                     Epar = Ech;
                     rhoP = rho;
                     zp = zp && (u == 0);
