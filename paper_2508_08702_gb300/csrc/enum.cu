@@ -304,9 +304,11 @@ struct Levels {
     __device__ __forceinline__ unsigned char& J(int t) const { return base[35 * K + t]; }
     // discrepancies on the path above level t (limited discrepancy search)
     __device__ __forceinline__ unsigned char& dab(int t) const { return base[36 * K + t]; }
+    // the queue item (prefix) of the current walk
+    __device__ __forceinline__ int64_t& gid() const { return *reinterpret_cast<int64_t*>(base + (37 * K + 7) / 8 * 8); }
 };
 
-__host__ __device__ inline int level_bytes(int Kmax) { return (Kmax * 37 + 15) / 16 * 16; }
+__host__ __device__ inline int level_bytes(int Kmax) { return ((37 * Kmax + 7) / 8 * 8 + 8 + 15) / 16 * 16; }
 
 __device__ __forceinline__ Levels levels_at(unsigned char* base, int Kmax) {
     Levels L;
@@ -706,8 +708,8 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     bool static_done = false;          // lane 0: the split queue is exhausted
     int idle_reg = 0;                  // counted in ctrl->idle (uniform over the group)
     int inst = 0, dd = 0, dim = 0, sx = 0, Sf = 0, t0 = 0, t = 0;
-    int64_t gid = 0;
-    long long Rbits = 0, eps_fix = 0, ehalf = 0;
+    long long Rbits = 0, eps_fix = 0;
+    int ehalf = 0;
     long long rmax = 1;   // stays the constant 1 in the binary variant
     double eps = 0.0;
     const double* muT = nullptr;
@@ -723,7 +725,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     int bq[CPL];
 #pragma unroll
     for (int q = 0; q < CPL; ++q) { W[q] = 0; bq[q] = 0; }
-    unsigned long long nodes = 0, passed = 0, cfma = 0;
+    unsigned nodes = 0, passed = 0, cfma = 0;   // per walk, flushed before they could overflow
     unsigned leaves = 0, fallbacks = 0, cuts = 0;
     int item_sols = 0;
     unsigned spins = 0;
@@ -734,6 +736,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
         // ================= fetch: one non-blocking attempt per step =========
         // (a walker already waiting for donated work polls every 32nd step)
         if (state == kFetch && (!idle_reg || ((++spins & 31) == 0))) {
+            int64_t gid = 0;   // this step's queue item (kept in shared memory for the walk)
             int src = 0, quit = 0;
             long long id = 0;
             if (lg == 0) {
@@ -793,6 +796,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 // ---- set up a walk ----
                 if (src == 1) {
                     gid = P.qperm ? P.qperm[id] : (int64_t)id;
+                    if (lg == 0) L.gid() = gid;
                     int lo = 0, hi = P.count;
                     while (hi - lo > 1) {
                         const int mid = (lo + hi) >> 1;
@@ -803,6 +807,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     const DonHdr* hd = reinterpret_cast<const DonHdr*>(P.don + id * P.don_stride);
                     inst = hd->inst;
                     gid = hd->gid;
+                    if (lg == 0) L.gid() = gid;
                 }
                 int skip = 0;
                 if (cfg.first && lg == 0) skip = *(volatile unsigned*)&P.gsolved[P.inst[inst].group] != 0;
@@ -885,7 +890,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     const int c = lg + G * q;
                     W[q] = (c < dim) ? llrint(ldexp(root_w[c], Sf)) : 0LL;
                 }
-                Epar = ehalf;
+                Epar = (long long)ehalf;
                 t = t0;
                 Bt = Btab[t];
                 nbq_t = nbqtab[t];
@@ -917,7 +922,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     srow[i] = acc;
                 }
                 y = acc;
-                cfma += (unsigned long long)(Jt - t);
+                cfma += (unsigned)(Jt - t);
                 if (lg == 0) {
                     if (t > 0 && L.J(t - 1) < max(Jt, t)) L.J(t - 1) = (unsigned char)max(Jt, t);
                     L.J(t) = (unsigned char)t;
@@ -957,7 +962,24 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 if (__shfl_sync(gmask, st, 0, G)) abort = true;
                 else if (__shfl_sync(gmask, solved, 0, G)) { abort = true; quiet = true; }
                 else if (__shfl_sync(gmask, want, 0, G))
-                    donate<G>(P, inst, gid, L, root_w, P.bhat + P.inst[inst].offBhat, t0, t, dd, dim, Kmax, cfg.lds, gmask);
+                    donate<G>(P, inst, L.gid(), L, root_w, P.bhat + P.inst[inst].offBhat, t0, t, dd, dim, Kmax, cfg.lds,
+                              gmask);
+                // the 32-bit walk counters are flushed long before they could wrap
+                // (at most 1024 nodes and 1024 x 128 centre fmas between checks)
+                if (nodes >= (1u << 30) || cfma >= (1u << 30)) {
+                    if (lg == 0) {
+                        atomicAdd(&P.cnt[inst].nodes, (unsigned long long)nodes);
+                        atomicAdd(&P.cnt[inst].passed, (unsigned long long)passed);
+                        atomicAdd(&P.cnt[inst].leaves, (unsigned long long)leaves);
+                        atomicAdd(&P.cnt[inst].center_fma, (unsigned long long)cfma);
+                        atomicAdd(&P.cnt[inst].fallbacks, (unsigned long long)fallbacks);
+                        if (cuts) atomicAdd(&P.cnt[inst].lds_cuts, (unsigned long long)cuts);
+                        atomicAdd(reinterpret_cast<unsigned long long*>(&P.plog_nodes[L.gid()]),
+                                  (unsigned long long)nodes);
+                    }
+                    nodes = passed = cfma = 0;
+                    leaves = fallbacks = cuts = 0;
+                }
             }
             if (u >= kUMax || u <= -kUMax) {
                 if (!abort && lg == 0) set_status(P.inst[inst], ST_EOVERFLOW);
@@ -995,12 +1017,12 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
 #pragma unroll
                         for (int off = G / 2; off >= 1; off >>= 1) lsum += __shfl_xor_sync(gmask, lsum, off, G);
                         const long long axq = xq < 0 ? -(long long)xq : (long long)xq;
-                        Ech = Epar + ((ehalf * (axq + 1)) >> 1) + nbq_t + 1;
+                        Ech = Epar + (((long long)ehalf * (axq + 1)) >> 1) + nbq_t + 1;
                         bool fail = false;
                         if (cfg.hoelder != HOELDER_OFF) {
                             // r_max ||w||_1 (Theorem 2 with r_max); r_max = 1 for binary problems
                             long long Lfix = (long long)lsum << kHiShift;
-                            long long Ebase = Ech + (Ech >> 10) + (ehalf << kHiShift);
+                            long long Ebase = Ech + (Ech >> 10) + ((long long)ehalf << kHiShift);
                             if (BND && rmax != 1) { Lfix *= rmax; Ebase *= rmax; }
                             const long long M = fix_trunc(rho, Sf) - Lfix - eps_fix;
                             const long long Etot = Ebase + (Lfix >> 32) + 64;
@@ -1079,7 +1101,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                             bq[q] = (lg + G * q < dim) ? bqtab[(int64_t)t * dimPad + lg + G * q] : 0;
                             W[q] -= (long long)xqt * (long long)bq[q];
                         }
-                        Epar -= ((ehalf * (axt + 1)) >> 1) + nbq_t + 1;
+                        Epar -= (((long long)ehalf * (axt + 1)) >> 1) + nbq_t + 1;
                         if (!(meta & kDonated)) break;
                     }
                     if (!finished) {
@@ -1100,14 +1122,14 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
             if (finished) {
                 if (lg == 0) {
                     if (abort && !quiet && !(*(volatile unsigned*)&ctrl->stop)) set_status(P.inst[inst], ST_EOVERFLOW);
-                    atomicAdd(&P.cnt[inst].nodes, nodes);
-                    atomicAdd(&P.cnt[inst].passed, passed);
+                    atomicAdd(&P.cnt[inst].nodes, (unsigned long long)nodes);
+                    atomicAdd(&P.cnt[inst].passed, (unsigned long long)passed);
                     atomicAdd(&P.cnt[inst].leaves, (unsigned long long)leaves);
-                    atomicAdd(&P.cnt[inst].center_fma, cfma);
+                    atomicAdd(&P.cnt[inst].center_fma, (unsigned long long)cfma);
                     atomicAdd(&P.cnt[inst].fallbacks, (unsigned long long)fallbacks);
                     if (cuts) atomicAdd(&P.cnt[inst].lds_cuts, (unsigned long long)cuts);
-                    atomicAdd(reinterpret_cast<unsigned long long*>(&P.plog_nodes[gid]), nodes);
-                    if (item_sols) atomicAdd(&P.plog_sols[gid], item_sols);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&P.plog_nodes[L.gid()]), (unsigned long long)nodes);
+                    if (item_sols) atomicAdd(&P.plog_sols[L.gid()], item_sols);
                     atomicAdd(&ctrl->walk_cycles, (unsigned long long)(clock64() - walk0));
                     atomicSub(&ctrl->busy, 1);
                 }
