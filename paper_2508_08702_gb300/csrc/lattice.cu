@@ -129,14 +129,17 @@ __device__ __forceinline__ double pick4(const double (&a)[4], int q) {
 }
 
 // Row k of the Gram-Schmidt data from the exact Gram matrix.  Lane l owns the
-// columns j = l + 32 q (q < 4).  mu_at(j, i) returns mu_ji for j < k.
-// Results: rrow[i] = r_ki, murow[i] = mu_ki (i < k), *Bk = r_kk.
+// columns j = l + 32 q (q < 4).  mu_at(j, i) returns mu_ji for j < k; it
+// should read a layout where fixed i and consecutive j are adjacent (the
+// lanes of a step then read one coalesced row).
+// Results: rrow[i] = r_ki (when rrow is given), murow[i * mstride] = mu_ki
+// (i < k), *Bk = r_kk.
 // With invB (the reduction), mu_ki = r_ki * invB[i] and invB[k] = 1 / r_kk is
 // stored; without it (Eq. (4) for the enumeration tables), mu_ki = r_ki / B[i].
 template <class MuAt>
 __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ Grow, MuAt mu_at,
                                              const double* __restrict__ B, double* rrow, double* murow,
-                                             double* Bk, int lane, double* invB = nullptr) {
+                                             int mstride, double* Bk, int lane, double* invB = nullptr) {
     double acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -154,7 +157,7 @@ __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ 
         }
         if (lane == 0) {
             if (rrow) rrow[i] = rki;
-            murow[i] = muki;
+            murow[(int64_t)i * mstride] = muki;
         }
     }
     const double rkk = __shfl_sync(kFull, pick4(acc, k >> 5), k & 31);
@@ -180,7 +183,9 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
                             double delta, double eta, int64_t max_iter, unsigned long long deadline_ns,
                             int64_t& iters, int64_t& swaps, int k0 = 0, int* lo = nullptr) {
     const int lane = threadIdx.x & 31;
-    auto mu_at = [&](int j, int i) { return mu[(int64_t)j * K + i]; };
+    // mu stored transposed: mu[i * K + j] = mu_ji (coalesced Gram-Schmidt rows)
+    auto mu_at = [&](int j, int i) { return mu[(int64_t)i * K + j]; };
+    (void)r;
     int32_t st = ST_OK;
     int64_t it = 0;
     int low = K;
@@ -197,7 +202,7 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
         }
         if (__any_sync(kFull, ovf)) st = ST_EOVERFLOW;
         __syncwarp();
-        if (st == ST_OK) gso_row_warp(0, G, mu_at, B, r, mu, &B[0], lane, invB);
+        if (st == ST_OK) gso_row_warp(0, G, mu_at, B, nullptr, mu, K, &B[0], lane, invB);
     }
 
     int k = k0 > 1 ? k0 : 1;
@@ -210,17 +215,16 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
         // lazy size reduction of b_k
         for (int pass = 0;; ++pass) {
             if (pass > 1000) { st = ST_ECAP; break; }
-            gso_row_warp(k, G + (int64_t)k * K, mu_at, B, r + (int64_t)k * K, mu + (int64_t)k * K, &B[k], lane,
-                         invB);
+            gso_row_warp(k, G + (int64_t)k * K, mu_at, B, nullptr, mu + k, K, &B[k], lane, invB);
             bool changed = false, ovf = false;
             for (int j = k - 1; j >= 0; --j) {
-                const double mkj = mu[(int64_t)k * K + j];
+                const double mkj = mu[(int64_t)j * K + k];
                 if (fabs(mkj) > eta) {
                     const double qd = rint(mkj);
                     if (fabs(qd) > 4503599627370496.0) { ovf = true; break; }
                     const int64_t q = (int64_t)qd;
                     for (int i = lane; i < j; i += 32)
-                        mu[(int64_t)k * K + i] = __fma_rn(-qd, mu[(int64_t)j * K + i], mu[(int64_t)k * K + i]);
+                        mu[(int64_t)i * K + k] = __fma_rn(-qd, mu[(int64_t)i * K + j], mu[(int64_t)i * K + k]);
                     int64_t* bk = b + (int64_t)k * L;
                     const int64_t* bj = b + (int64_t)j * L;
                     for (int c = lane; c < L; c += 32) {
@@ -229,7 +233,7 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
                         bk[c] = (int64_t)v;
                     }
                     __syncwarp();
-                    if (lane == 0) mu[(int64_t)k * K + j] = __dsub_rn(mkj, qd);
+                    if (lane == 0) mu[(int64_t)j * K + k] = __dsub_rn(mkj, qd);
                     __syncwarp();
                     changed = true;
                     if (__any_sync(kFull, ovf)) break;
@@ -249,7 +253,7 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
         }
         if (st != ST_OK) break;
         // Lovasz condition
-        const double mk = mu[(int64_t)k * K + (k - 1)];
+        const double mk = mu[(int64_t)(k - 1) * K + k];
         const double t1 = __dmul_rn(mk, mk);
         const double t2 = __dsub_rn(delta, t1);
         const double rhs = __dmul_rn(t2, B[k - 1]);
@@ -273,7 +277,7 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
             __syncwarp();
             ++swaps;
             low = min(low, k - 1);
-            if (k - 1 == 0) gso_row_warp(0, G, mu_at, B, r, mu, &B[0], lane, invB);
+            if (k - 1 == 0) gso_row_warp(0, G, mu_at, B, nullptr, mu, K, &B[0], lane, invB);
             k = (k > 1) ? k - 1 : 1;
         } else {
             ++k;
@@ -405,7 +409,7 @@ __global__ void __launch_bounds__(32) extract_gso_kernel(Pools P, int gso_only) 
     double* murow = rrow + K;         // scratch row
     auto mu_at = [&](int j, int i) { return muT[(int64_t)i * dd + j]; };
     for (int i = 0; i < dd; ++i) {
-        gso_row_warp(i, G + (int64_t)i * dd, mu_at, Bt, rrow, murow, &Bt[i], lane);
+        gso_row_warp(i, G + (int64_t)i * dd, mu_at, Bt, rrow, murow, 1, &Bt[i], lane);
         for (int j = lane; j < dd; j += 32)
             muT[(int64_t)j * dd + i] = (j < i) ? murow[j] : (j == i ? 1.0 : 0.0);
         __syncwarp();
@@ -486,7 +490,7 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
     int32_t* flg = ziv + K;                                       // bit 0 zero prefix, bit 1 negative side
     int32_t* kb = P.kb + I.offKb;
     const unsigned long long deadline = __shfl_sync(kFull, global_time_ns(), 0) + max_ns;   // uniform
-    auto mu_at = [&](int j, int i) { return mu[(int64_t)j * dd + i]; };
+    auto mu_at = [&](int j, int i) { return mu[(int64_t)i * dd + j]; };   // transposed: mu[i dd + j] = mu_ji
 
     for (int e = lane; e < dd * dim; e += 32) b[e] = kb[e];
     __syncwarp();
@@ -516,8 +520,7 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
             // Gram-Schmidt rows of the changed part of the basis (Eq. (4), divided form)
             if (gso_lo < dd) {
                 for (int i = gso_lo; i < dd; ++i)
-                    gso_row_warp(i, G + (int64_t)i * dd, mu_at, B, r + (int64_t)i * dd, mu + (int64_t)i * dd, &B[i],
-                                 lane);
+                    gso_row_warp(i, G + (int64_t)i * dd, mu_at, B, nullptr, mu + i, dd, &B[i], lane);
                 bool badB = false;   // a level with B_t <= 0 would never end its zig-zag
                 for (int i = lane; i < dd; i += 32) badB |= !(B[i] > 0.0 && B[i] < 1e300);
                 if (__any_sync(kFull, badB)) { st = ST_EOVERFLOW; break; }
@@ -538,7 +541,7 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
                         bool zp = true;
                         for (int i = t + 1; i < h; ++i) if (u[i] != 0) { zp = false; break; }
                         double acc = 0.0;
-                        for (int i = h - 1; i > t; --i) acc = __fma_rn((double)u[i], mu[(int64_t)i * dd + t], acc);
+                        for (int i = h - 1; i > t; --i) acc = __fma_rn((double)u[i], mu[(int64_t)t * dd + i], acc);
                         yv[t] = acc;
                         const double cstar = -acc;
                         const double r1 = rint(cstar);
