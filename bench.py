@@ -34,7 +34,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "enum nodes/s; time to all sols (m=9) & first sol (m=12), learned vs plain order"
-DRAM_BYTES_PER_NODE = (113.761024e6 + 465.414144e6) / 268321291   # enum_kernel<8, 8>, ncu
+DRAM_BYTES_PER_NODE = (104.385280e6 + 337.268992e6) / 268321291   # enum_kernel<8, 8, 0>, ncu
 UNIT = "nodes/s"
 WORKLOAD = "batch of 64 fMSP instances, m~U{4..7}, n=10(m-1), D in {50,100,200}, all solutions"
 
