@@ -361,6 +361,38 @@ __device__ __forceinline__ long long fix_trunc(double x, int s) {
     return b < 0 ? -q : q;
 }
 
+// The start of a level's zig-zag from its centre y, on the bit pattern of
+// c = -y with integer operations only (an FP64 operation costs ~64 cycles of
+// latency on this GPU): u1 = c rounded to nearest, ties to even (rint), and
+// the side s = +1 if c >= u1 else -1.  Returns true when |u1| >= kUMax.
+__device__ __forceinline__ bool centre_round(double y, int& u1, int& s) {
+    const unsigned long long c = (unsigned long long)__double_as_longlong(y) ^ 0x8000000000000000ULL;   // -y
+    const bool neg = (c >> 63) != 0;
+    const int e = (int)((c >> 52) & 0x7ff);
+    const unsigned long long frac = c & 0x000fffffffffffffULL;
+    unsigned long long mag;
+    bool up, exact;
+    if (e >= 1023 + 16) return true;   // |c| >= 2^16
+    const int shift = 1075 - e;        // >= 21: the integer part has at most 32 bits
+    if (e == 0 || shift > 63) {        // |c| < 2^-11 (or zero, or subnormal): rounds to 0
+        mag = 0;
+        up = false;
+        exact = (e == 0 && frac == 0);
+    } else {
+        const unsigned long long m = frac | 0x0010000000000000ULL;
+        const unsigned long long ip = m >> shift;
+        const unsigned long long rem = m & ((1ULL << shift) - 1ULL);
+        const unsigned long long half = 1ULL << (shift - 1);
+        up = rem > half || (rem == half && (ip & 1ULL));
+        exact = rem == 0;
+        mag = ip + (up ? 1ULL : 0ULL);
+    }
+    if (mag >= (unsigned long long)kUMax) return true;
+    u1 = neg ? -(int)mag : (int)mag;
+    s = neg ? ((up || exact) ? 1 : -1) : (up ? -1 : 1);
+    return false;
+}
+
 // level meta bits
 constexpr int kOneDir = 1, kNegS = 2, kZeroPrefix = 4, kDonated = 8;
 
@@ -927,11 +959,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     if (t > 0 && L.J(t - 1) < max(Jt, t)) L.J(t - 1) = (unsigned char)max(Jt, t);
                     L.J(t) = (unsigned char)t;
                 }
-                const double cstar = -y;
-                const double r1 = rint(cstar);
-                if (fabs(r1) >= (double)kUMax) abort = true;
-                u1 = abort ? 0 : (int)r1;
-                s = (cstar >= r1) ? 1 : -1;
+                if (centre_round(y, u1, s)) { abort = true; u1 = 0; s = 1; }
                 onedir = false; dir = 0; zi = 1;
                 if (zp && cfg.sym) { u1 = 0; onedir = true; dir = 1; }
                 u = u1;
