@@ -59,7 +59,10 @@
  *       G ("lanes") is a parameter; G = 1 is the sequential sum.
  *   R10 N = 2^10 (Sec. 2); delta = 0.99, eta = 0.51 (the paper gives neither);
  *       inside LLL mu_kj = r_kj (1/B_j) with the reciprocal formed once per
- *       row, in the enumeration tables mu = r / B (Eq. (4) as written).
+ *       row, in the enumeration tables mu = r / B (Eq. (4) as written).  Size
+ *       reduction of a row: one pass j = k-1 .. 0 on its freshly computed
+ *       Gram-Schmidt row, updated in place; the LLL inside BKZ repeats the
+ *       pass until nothing changes (see oracle_lll).
  *   R11 Instances are made feasible by a planted binary x, d = A x (the
  *       construction of the paper's instance library is not described).
  *   R12 Limited discrepancy search (Sec. 3, after Harvey and Ginsberg): a
@@ -192,9 +195,15 @@ static int gram_row(int k, int K, int L, const int64_t *b, int64_t *G)
 }
 
 /* delta-LLL with size-reduction parameter eta.  b is K vectors of length L,
- * reduced in place.  Returns OR_OK, OR_EOVERFLOW or OR_ECAP (iteration cap). */
-int oracle_lll(int K, int L, int64_t *b, double delta, double eta, int64_t max_iter,
-               int64_t *iters_out, int64_t *swaps_out)
+ * reduced in place.  Returns OR_OK, OR_EOVERFLOW or OR_ECAP (iteration cap).
+ * Size reduction of row k (R10): its Gram-Schmidt row is computed from the
+ * exact Gram matrix, then mu_kj for j = k-1 .. 0 is reduced in one pass,
+ * the reductions updating the row in place (fma); the Gram row of b_k is
+ * recomputed exactly.  lazy != 0 (the LLL inside BKZ) repeats the pass on a
+ * freshly computed row until nothing changes, so the stored rows of a
+ * finished run always equal a fresh computation. */
+static int lll_core(int K, int L, int64_t *b, double delta, double eta, int64_t max_iter,
+                    int64_t *iters_out, int64_t *swaps_out, int lazy)
 {
     int st = OR_OK;
     int64_t *G = (int64_t *)calloc((size_t)K * K, sizeof(int64_t));
@@ -212,7 +221,7 @@ int oracle_lll(int K, int L, int64_t *b, double delta, double eta, int64_t max_i
     int k = 1;
     while (k < K) {
         if (++iters > max_iter) { st = OR_ECAP; goto done; }
-        /* lazy size reduction: reduce, recompute the row exactly, repeat */
+        /* size reduction (lazy: reduce, recompute the row exactly, repeat) */
         for (int pass = 0;; ++pass) {
             if (pass > 1000) { st = OR_ECAP; goto done; }
             gso_row(k, K, G, mu, r, B, invB);
@@ -238,6 +247,7 @@ int oracle_lll(int K, int L, int64_t *b, double delta, double eta, int64_t max_i
             }
             if (!changed) break;
             if ((st = gram_row(k, K, L, b, G))) goto done;
+            if (!lazy) break;
         }
         /* Lovasz condition B_k >= (delta - mu_{k,k-1}^2) B_{k-1} */
         double mk = mu[(size_t)k * K + (k - 1)];
@@ -269,6 +279,12 @@ done:
     if (swaps_out) *swaps_out = swaps;
     free(G); free(mu); free(r); free(B); free(invB);
     return st;
+}
+
+int oracle_lll(int K, int L, int64_t *b, double delta, double eta, int64_t max_iter,
+               int64_t *iters_out, int64_t *swaps_out)
+{
+    return lll_core(K, L, b, delta, eta, max_iter, iters_out, swaps_out, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -731,7 +747,7 @@ int oracle_bkz(int dd, int dim, int64_t *b, int beta, double delta, int max_tour
             if (a[0] != 1 && a[0] != -1) continue;   /* not primitive: cannot be a basis vector */
             if (a[0] == -1) for (int c = 0; c < dim; ++c) rows[c] = -rows[c];
             memcpy(b + (size_t)k * dim, rows, sizeof(int64_t) * (size_t)(h - k) * dim);
-            if ((st = oracle_lll(dd, dim, b, delta, 0.51, lll_max_iter, NULL, NULL))) goto done;
+            if ((st = lll_core(dd, dim, b, delta, 0.51, lll_max_iter, NULL, NULL, 1))) goto done;
             ++inserts;
             inserted = 1;
         }

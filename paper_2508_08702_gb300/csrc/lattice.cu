@@ -171,7 +171,11 @@ __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ 
 
 // delta-LLL of K vectors of length L (int64, vector-major, in place) by one
 // warp: exact Gram matrix G (K x K), FP64 Gram-Schmidt rows recomputed from
-// it (mu, r: K x K; invB, B: K), lazy size reduction, Lovasz swaps.
+// it (mu: K x K; invB, B: K), size reduction, Lovasz swaps.  Size reduction
+// of row k: one pass j = k-1 .. 0 on its fresh Gram-Schmidt row, updated in
+// place; lazy (the LLL inside BKZ) repeats the pass on a fresh row until
+// nothing changes, so the stored rows of a finished run equal a fresh
+// computation (which the restart below relies on).
 // Returns a status; iterations and swaps are added to the counters.
 //
 // Restart (k0 > 0): G is the Gram matrix of the current basis and rows
@@ -181,7 +185,7 @@ __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ 
 __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, double* __restrict__ mu,
                             double* __restrict__ r, double* __restrict__ invB, double* __restrict__ B, int K, int L,
                             double delta, double eta, int64_t max_iter, unsigned long long deadline_ns,
-                            int64_t& iters, int64_t& swaps, int k0 = 0, int* lo = nullptr) {
+                            int64_t& iters, int64_t& swaps, int k0 = 0, int* lo = nullptr, bool lazy = false) {
     const int lane = threadIdx.x & 31;
     // mu stored transposed: mu[i * K + j] = mu_ji (coalesced Gram-Schmidt rows)
     auto mu_at = [&](int j, int i) { return mu[(int64_t)i * K + j]; };
@@ -250,6 +254,7 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
             }
             if (__any_sync(kFull, ovf)) { st = ST_EOVERFLOW; break; }
             __syncwarp();
+            if (!lazy) break;   // one pass; the lazy variant re-checks a fresh row
         }
         if (st != ST_OK) break;
         // Lovasz condition
@@ -648,7 +653,7 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
             // restart at k
             int lo = dd;
             st = lll_warp(b, G, mu2, r2, invB2, B2, dd, dim, delta, 0.51, lll_max_iter, deadline, iters, swaps,
-                          lll_state ? k : 0, &lo);
+                          lll_state ? k : 0, &lo, true);
             lll_state = true;
             small = rows_small(b, 0, dd, dim);
             gso_lo = min(gso_lo, min(k, lo));
