@@ -611,7 +611,8 @@ int oracle_enumerate_bounds(int dd, int dim, const double *mu, const double *B, 
 /*     coefficient g one row up; then row k equals the inserted vector and */
 /*     the whole basis is LLL-reduced again (delta, eta = 0.51).           */
 /*   - Tours repeat until one inserts nothing, or max_tours.               */
-/*   - GSO per block from the exact Gram matrix, divided form of Eq. (4).  */
+/*   - Gram-Schmidt data of the whole basis from the exact Gram matrix in   */
+/*     the LLL's form (mu_ij = r_ij (1/B_j)), rebuilt before each block.    */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int dd, h, k;
@@ -678,18 +679,20 @@ int oracle_bkz(int dd, int dim, int64_t *b, int beta, double delta, int max_tour
     double *mu = (double *)calloc((size_t)dd * dd, sizeof(double));
     double *r = (double *)calloc((size_t)dd * dd, sizeof(double));
     double *B = (double *)calloc((size_t)dd, sizeof(double));
+    double *invB = (double *)calloc((size_t)dd, sizeof(double));
     int64_t *G = (int64_t *)calloc((size_t)dd * dd, sizeof(int64_t));
     int64_t *rows = (int64_t *)calloc((size_t)dd * dim, sizeof(int64_t));
     int32_t *u = (int32_t *)calloc((size_t)dd, sizeof(int32_t));
     int32_t *best = (int32_t *)calloc((size_t)dd, sizeof(int32_t));
     int64_t *a = (int64_t *)calloc((size_t)dd, sizeof(int64_t));
-    if (!mu || !r || !B || !G || !rows || !u || !best || !a) { st = OR_ENOMEM; goto done; }
+    if (!mu || !r || !B || !invB || !G || !rows || !u || !best || !a) { st = OR_ENOMEM; goto done; }
     for (int tour = 0; tour < max_tours; ++tour) {
         int inserted = 0;
         ++tours;
         for (int k = 0; k + 1 < dd; ++k) {
             const int h = (k + beta < dd) ? k + beta : dd;
-            /* GSO of the current basis (exact Gram, Eq. (4) divided form) */
+            /* GSO of the current basis from the exact Gram matrix, in the
+             * LLL's form (mu_ij = r_ij (1/B_j), R14) */
             for (int i = 0; i < dd; ++i)
                 for (int j = 0; j <= i; ++j) {
                     int64_t g;
@@ -697,17 +700,7 @@ int oracle_bkz(int dd, int dim, int64_t *b, int beta, double delta, int max_tour
                     G[(size_t)i * dd + j] = g;
                     G[(size_t)j * dd + i] = g;
                 }
-            for (int i = 0; i < dd; ++i) {
-                for (int j = 0; j < i; ++j) {
-                    double acc = (double)G[(size_t)i * dd + j];
-                    for (int q = 0; q < j; ++q) acc = fma(-mu[(size_t)j * dd + q], r[(size_t)i * dd + q], acc);
-                    r[(size_t)i * dd + j] = acc;
-                    mu[(size_t)i * dd + j] = acc / B[j];
-                }
-                double acc = (double)G[(size_t)i * dd + i];
-                for (int q = 0; q < i; ++q) acc = fma(-mu[(size_t)i * dd + q], r[(size_t)i * dd + q], acc);
-                B[i] = acc;
-            }
+            for (int i = 0; i < dd; ++i) gso_row(i, dd, G, mu, r, B, invB);
             /* shortest nonzero vector of the projected block */
             svp_state e;
             memset(&e, 0, sizeof e);
@@ -757,7 +750,7 @@ done:
     if (tours_out) *tours_out = tours;
     if (inserts_out) *inserts_out = inserts;
     if (nodes_out) *nodes_out = nodes;
-    free(mu); free(r); free(B); free(G); free(rows); free(u); free(best); free(a);
+    free(mu); free(r); free(B); free(invB); free(G); free(rows); free(u); free(best); free(a);
     return st;
 }
 

@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
     int32_t* flg = ziv + K;                                       // bit 0 zero prefix, bit 1 negative side
     int32_t* kb = P.kb + I.offKb;
     const unsigned long long deadline = __shfl_sync(kFull, global_time_ns(), 0) + max_ns;   // uniform
-    auto mu_at = [&](int j, int i) { return mu[(int64_t)i * dd + j]; };   // transposed: mu[i dd + j] = mu_ji
+
 
     for (int e = lane; e < dd * dim; e += 32) b[e] = kb[e];
     __syncwarp();
@@ -515,26 +515,28 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
         if (__any_sync(kFull, ovf)) st = ST_EOVERFLOW;
         __syncwarp();
     }
-    int gso_lo = 0;          // Eq. (4) rows gso_lo .. dd-1 are stale
-    bool lll_state = false;  // mu2, r2, invB2, B2 hold an LLL fixed point of b
+    // Gram-Schmidt rows of the whole basis in the LLL's form (mu2, invB2, B2;
+    // mu2 transposed): fresh here, and kept fresh by the LLL runs below (the
+    // lazy LLL leaves every row as a fresh computation from the Gram matrix)
+    auto mu2_at = [&](int j, int i) { return mu2[(int64_t)i * dd + j]; };
+    if (st == ST_OK)
+        for (int i = 0; i < dd; ++i)
+            gso_row_warp(i, G + (int64_t)i * dd, mu2_at, B2, nullptr, mu2 + i, dd, &B2[i], lane, invB2);
+    bool lll_state = false;  // b is an LLL fixed point (a first LLL run has happened)
     for (int tour = 0; tour < max_tours && st == ST_OK; ++tour) {
         ++tours;
         bool inserted = false;
         for (int k = 0; k + 1 < dd && st == ST_OK; ++k) {
             const int h = min(k + beta, dd);
-            // Gram-Schmidt rows of the changed part of the basis (Eq. (4), divided form)
-            if (gso_lo < dd) {
-                for (int i = gso_lo; i < dd; ++i)
-                    gso_row_warp(i, G + (int64_t)i * dd, mu_at, B, nullptr, mu + i, dd, &B[i], lane);
+            {
                 bool badB = false;   // a level with B_t <= 0 would never end its zig-zag
-                for (int i = lane; i < dd; i += 32) badB |= !(B[i] > 0.0 && B[i] < 1e300);
+                for (int i = lane; i < dd; i += 32) badB |= !(B2[i] > 0.0 && B2[i] < 1e300);
                 if (__any_sync(kFull, badB)) { st = ST_EOVERFLOW; break; }
-                gso_lo = dd;
             }
             // shortest nonzero vector of the projected block (lane 0)
             int found = 0;
             if (lane == 0) {
-                double A = __dmul_rn(delta, B[k]);
+                double A = __dmul_rn(delta, B2[k]);
                 for (int i = 0; i < dd; ++i) u[i] = 0;
                 int t = h - 1;
                 rhoP[t] = 0.0;
@@ -546,7 +548,7 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
                         bool zp = true;
                         for (int i = t + 1; i < h; ++i) if (u[i] != 0) { zp = false; break; }
                         double acc = 0.0;
-                        for (int i = h - 1; i > t; --i) acc = __fma_rn((double)u[i], mu[(int64_t)t * dd + i], acc);
+                        for (int i = h - 1; i > t; --i) acc = __fma_rn((double)u[i], mu2[(int64_t)t * dd + i], acc);
                         yv[t] = acc;
                         const double cstar = -acc;
                         const double r1 = rint(cstar);
@@ -572,7 +574,7 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
                         }
                     }
                     const double x = __dadd_rn((double)cur, yv[t]);
-                    const double rho = __fma_rn(__dmul_rn(x, x), B[t], rhoP[t]);
+                    const double rho = __fma_rn(__dmul_rn(x, x), B2[t], rhoP[t]);
                     ++nloc;
                     if ((nloc & 4095) == 0 && global_time_ns() > deadline) { st = ST_ECAP; break; }
                     if (!(rho < A)) {   // level exhausted: back to the parent
@@ -656,7 +658,7 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
                           lll_state ? k : 0, &lo, true);
             lll_state = true;
             small = rows_small(b, 0, dd, dim);
-            gso_lo = min(gso_lo, min(k, lo));
+            (void)lo;
             ++inserts;
             inserted = true;
         }
