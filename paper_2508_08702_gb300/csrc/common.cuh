@@ -133,16 +133,16 @@ struct Ctrl {
 
 // Enumeration options passed to the split and enumeration kernels.
 // Per-instance global scratch of the BKZ kernel: two K x D int64 blocks
-// (basis, block copy), five K x K blocks (Gram; mu, r of Eq. (4); mu, r of
-// the LLL), eight K-vectors of 8 bytes and five of 4 bytes; the stride is
-// rounded to 256 bytes.
+// (basis, block copy), three K x K blocks (Gram; the LLL's mu and r), five
+// K-vectors of 8 bytes and five of 4 bytes; the stride is rounded to 256
+// bytes.
 struct BkzScratch {
     char* base;
     int64_t stride;   // bytes per instance
     int Kmax, dimMax;
     __host__ __device__ static int64_t bytes(int Kmax, int dimMax) {
         const int64_t K = Kmax, D = dimMax;
-        const int64_t raw = 8 * (2 * K * D + 5 * K * K + 8 * K) + 4 * 5 * K;
+        const int64_t raw = 8 * (2 * K * D + 3 * K * K + 5 * K) + 4 * 5 * K;
         return (raw + 255) / 256 * 256;
     }
 };

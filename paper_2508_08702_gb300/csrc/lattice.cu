@@ -181,18 +181,17 @@ __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ 
 // Restart (k0 > 0): G is the Gram matrix of the current basis and rows
 // 0 .. k0-1 are an LLL fixed point whose Gram-Schmidt rows (mu, r, invB, B)
 // are in place -- a run from scratch would pass them unchanged, so starting
-// at k0 gives the same result.  *lo receives the lowest row changed.
+// at k0 gives the same result.
 __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, double* __restrict__ mu,
                             double* __restrict__ r, double* __restrict__ invB, double* __restrict__ B, int K, int L,
                             double delta, double eta, int64_t max_iter, unsigned long long deadline_ns,
-                            int64_t& iters, int64_t& swaps, int k0 = 0, int* lo = nullptr, bool lazy = false) {
+                            int64_t& iters, int64_t& swaps, int k0 = 0, bool lazy = false) {
     const int lane = threadIdx.x & 31;
     // mu stored transposed: mu[i * K + j] = mu_ji (coalesced Gram-Schmidt rows)
     auto mu_at = [&](int j, int i) { return mu[(int64_t)i * K + j]; };
     (void)r;
     int32_t st = ST_OK;
     int64_t it = 0;
-    int low = K;
     bool small = rows_small(b, 0, K, L);
     if (k0 <= 0) {   // exact Gram matrix
         bool ovf = false;
@@ -245,7 +244,6 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
             }
             if (__any_sync(kFull, ovf)) { st = ST_EOVERFLOW; break; }
             if (!changed) break;
-            low = min(low, k);
             small = small && rows_small(b, k, k + 1, L);
             for (int i = lane; i < K; i += 32) {
                 const int64_t g = dot_small(b + (int64_t)k * L, b + (int64_t)i * L, L, small, ovf);
@@ -281,7 +279,6 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
             }
             __syncwarp();
             ++swaps;
-            low = min(low, k - 1);
             if (k - 1 == 0) gso_row_warp(0, G, mu_at, B, nullptr, mu, K, &B[0], lane, invB);
             k = (k > 1) ? k - 1 : 1;
         } else {
@@ -289,7 +286,6 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
         }
     }
     iters += it;
-    if (lo) *lo = low;
     return st;
 }
 
@@ -476,26 +472,20 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
     int64_t* b = reinterpret_cast<int64_t*>(sp);                 // dd x dim
     int64_t* rows = b + (int64_t)K * D;                           // block copy
     int64_t* G = rows + (int64_t)K * D;                           // dd x dd, exact Gram of b
-    double* mu = reinterpret_cast<double*>(G + (int64_t)K * K);   // Eq. (4) rows (divided form)
-    double* r = mu + (int64_t)K * K;
-    double* mu2 = r + (int64_t)K * K;                             // the LLL's rows (reciprocal form)
-    double* r2 = mu2 + (int64_t)K * K;
-    double* B = r2 + (int64_t)K * K;
-    double* invB2 = B + K;
+    double* mu2 = reinterpret_cast<double*>(G + (int64_t)K * K);  // Gram-Schmidt rows, LLL's form, transposed
+    double* r2 = mu2 + (int64_t)K * K;                            // (unused by the reciprocal form)
+    double* invB2 = r2 + (int64_t)K * K;
     double* B2 = invB2 + K;
     double* yv = B2 + K;                                          // SVP: centre per level
     double* rhoP = yv + K;                                        // SVP: parent norm per level
-    int64_t* a = reinterpret_cast<int64_t*>(rhoP + K);
-    double* spare = reinterpret_cast<double*>(a + K);
-    double* spare2 = spare + K;
-    int32_t* u = reinterpret_cast<int32_t*>(spare2 + K);
+    int64_t* a = reinterpret_cast<int64_t*>(rhoP + K);            // insertion coefficients
+    int32_t* u = reinterpret_cast<int32_t*>(a + K);
     int32_t* best = u + K;
     int32_t* u1v = best + K;
     int32_t* ziv = u1v + K;
     int32_t* flg = ziv + K;                                       // bit 0 zero prefix, bit 1 negative side
     int32_t* kb = P.kb + I.offKb;
     const unsigned long long deadline = __shfl_sync(kFull, global_time_ns(), 0) + max_ns;   // uniform
-
 
     for (int e = lane; e < dd * dim; e += 32) b[e] = kb[e];
     __syncwarp();
@@ -653,12 +643,10 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
             // LLL of the whole basis: once a first run has made the basis an
             // LLL fixed point, the rows above k are untouched, so later runs
             // restart at k
-            int lo = dd;
             st = lll_warp(b, G, mu2, r2, invB2, B2, dd, dim, delta, 0.51, lll_max_iter, deadline, iters, swaps,
-                          lll_state ? k : 0, &lo, true);
+                          lll_state ? k : 0, true);
             lll_state = true;
             small = rows_small(b, 0, dd, dim);
-            (void)lo;
             ++inserts;
             inserted = true;
         }
