@@ -34,7 +34,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "enum nodes/s; time to all sols (m=9) & first sol (m=12), learned vs plain order"
-DRAM_BYTES_PER_NODE = (104.385280e6 + 337.268992e6) / 268321291   # enum_kernel<8, 8, 0>, ncu
+DRAM_BYTES_PER_NODE = (107.729664e6 + 333.254400e6) / 268321291   # enum_kernel<8, 8, 0>, ncu
 UNIT = "nodes/s"
 WORKLOAD = "batch of 64 fMSP instances, m~U{4..7}, n=10(m-1), D in {50,100,200}, all solutions"
 
@@ -66,6 +66,7 @@ WORKLOADS = {
     "m9_all": ("m9_n80", "all", 1200.0),    # m=9, n=80, D=100, 8 instances, 40 ones planted
     "m8_first": ("m8_n70", "first", 120.0),
     "m12_first": ("m12_n110", "first", 60.0),   # m=12, n=110, D=100, 4 instances
+    "m12d50_first": ("m12_n110_d50", "first", 60.0),   # m=12, n=110, D=50 (the paper's m=12 row), 4 instances
     "cd8_all": ("cd8", "all", 600.0),       # Cornuejols-Dawande m=8 (nothing planted), 16 instances
 }
 

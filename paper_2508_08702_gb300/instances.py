@@ -101,6 +101,12 @@ def m12_n110(count: int = 4) -> List[Instance]:
     return [make_instance(5000 + i, 12, 110, 100, tag=f"m12n110_{i}") for i in range(count)]
 
 
+def m12_n110_d50(count: int = 4) -> List[Instance]:
+    """m=12, n=110, D=50, seeds 5100.. (planted Bernoulli(1/2)): the shape of
+    the paper's only m = 12 row (D = 50)."""
+    return [make_instance(5100 + i, 12, 110, 50, tag=f"m12d50_{i}") for i in range(count)]
+
+
 def training_set(count: int = 256, first_seed: int = 30000) -> List[Instance]:
     """Training instances for the subtree scorer: m cycling 5,6,7, D cycling
     over {50, 100, 200}; seeds disjoint from every evaluation set."""
