@@ -717,9 +717,11 @@ enum : int { kFetch = 0, kWalk = 1, kDone = 2 };
 #define MSP_ENUM_MIN_BLOCKS(g) ((g) >= 8 ? 2 : 1)
 #endif
 
-// BND: the batch holds an instance with bounds beyond 0/1 (r_max > 1); the
-// binary variant keeps r_max = 1 as a compile-time constant.
-template <int G, int CPL, bool BND>
+// EXT: the extended walker -- the batch holds an instance with bounds beyond
+// 0/1 (r_max > 1) or the search is a limited-discrepancy iteration.  The
+// plain variant (binary, depth-first) keeps r_max = 1 and carries no
+// discrepancy bookkeeping, so its register budget stays with the hot loop.
+template <int G, int CPL, bool EXT>
 __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     enum_kernel(Pools P, EnumCfg cfg, char* scratch, WalkerLayout WL) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -866,7 +868,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 Btab = P.B + I.offB;
                 bqtab = P.bq + I.offBq;
                 nbqtab = P.nbq + I.offNbq;
-                if (BND) rmax = I.rmax;
+                if (EXT) rmax = I.rmax;
                 {
                     const double R = bound_R(I);
                     eps = slack_of(R, cfg.use_eps);
@@ -888,7 +890,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     }
                     for (int c = lg; c < dim; c += G) root_w[c] = P.fw[fo * P.dimPad + c];
                     rhoP = P.frho[fo];
-                    dab = P.fdisc[fo];
+                    if (EXT) dab = P.fdisc[fo];
                 } else {
                     const char* slot = P.don + id * P.don_stride;
                     const DonHdr hd = *reinterpret_cast<const DonHdr*>(slot);
@@ -912,7 +914,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     s = (hd.meta & kNegS) ? -1 : 1;
                     zp = (hd.meta & kZeroPrefix) != 0;
                     if (onedir) dir = hd.zi; else zi = hd.zi;
-                    dab = hd.dab;
+                    if (EXT) dab = hd.dab;
                 }
                 for (int i = lg; i <= t0; i += G) L.J(i) = (unsigned char)(dd - 1);
                 if (lg == 0) L.meta(t0) = 0;
@@ -990,7 +992,8 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 if (__shfl_sync(gmask, st, 0, G)) abort = true;
                 else if (__shfl_sync(gmask, solved, 0, G)) { abort = true; quiet = true; }
                 else if (__shfl_sync(gmask, want, 0, G))
-                    donate<G>(P, inst, L.gid(), L, root_w, P.bhat + P.inst[inst].offBhat, t0, t, dd, dim, Kmax, cfg.lds,
+                    donate<G>(P, inst, L.gid(), L, root_w, P.bhat + P.inst[inst].offBhat, t0, t, dd, dim, Kmax,
+                              EXT ? cfg.lds : -1,
                               gmask);
                 // the 32-bit walk counters are flushed long before they could wrap
                 // (at most 1024 nodes and 1024 x 128 centre fmas between checks)
@@ -1018,7 +1021,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 // ---- node (t, u): centre, norm (FP64, the canonical operations) ----
                 const double x = __dadd_rn(i2d_exact(u), y);
                 const double rho = __fma_rn(__dmul_rn(x, x), Bt, rhoP);
-                const bool over_budget = cfg.lds >= 0 && u != u1 && dab >= cfg.lds;
+                const bool over_budget = EXT && cfg.lds >= 0 && u != u1 && dab >= cfg.lds;
                 nodes += over_budget ? 0 : 1;
                 cuts += over_budget ? 1 : 0;
                 long long Ech = 0;
@@ -1029,8 +1032,8 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     ++passed;
                     if (t == 0) {
                         ++leaves;
-                        if (cfg.lds < 0 || dab + (u != u1 ? 1 : 0) == cfg.lds)
-                            item_sols += BND ? leaf_check_bounded<G, CPL>(P, cfg, inst, L, u, gmask)
+                        if (!EXT || cfg.lds < 0 || dab + (u != u1 ? 1 : 0) == cfg.lds)
+                            item_sols += EXT ? leaf_check_bounded<G, CPL>(P, cfg, inst, L, u, gmask)
                                              : leaf_check<G, CPL>(P, cfg, inst, L, u, gmask);
                         act = kNext;
                     } else {
@@ -1051,7 +1054,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                             // r_max ||w||_1 (Theorem 2 with r_max); r_max = 1 for binary problems
                             long long Lfix = (long long)lsum << kHiShift;
                             long long Ebase = Ech + (Ech >> 10) + ((long long)ehalf << kHiShift);
-                            if (BND && rmax != 1) { Lfix *= rmax; Ebase *= rmax; }
+                            if (EXT && rmax != 1) { Lfix *= rmax; Ebase *= rmax; }
                             const long long M = fix_trunc(rho, Sf) - Lfix - eps_fix;
                             const long long Etot = Ebase + (Lfix >> 32) + 64;
                             if (M > Etot) fail = true;
@@ -1081,6 +1084,14 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         }
                     }
                 }
+                // limited discrepancy search: once the path above has spent the
+                // budget, every further value of this level is over it -- leave
+                // the level now (one cut, as when the value is tried) instead of
+                // spending a step on it
+                if (EXT && cfg.lds >= 0 && (act == kNext || act == kEval) && dab >= cfg.lds) {
+                    ++cuts;
+                    act = kUp;
+                }
                 if (act == kDescend) {
                     // save level t; the child becomes the parent of level t-1
                     if (lg == 0) {
@@ -1092,9 +1103,9 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         L.xq(t) = xq;
                         L.y(t) = y;
                         L.rho(t) = rhoP;
-                        L.dab(t) = (unsigned char)dab;
+                        if (EXT) L.dab(t) = (unsigned char)dab;
                     }
-                    dab += (u != u1) ? 1 : 0;
+                    if (EXT) dab += (u != u1) ? 1 : 0;
 #pragma unroll
                     {
                         // the child's W = W + xq Bq, recomputed instead of keeping the
@@ -1130,7 +1141,11 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                             W[q] -= (long long)xqt * (long long)bq[q];
                         }
                         Epar -= (((long long)ehalf * (axt + 1)) >> 1) + nbq_t + 1;
-                        if (!(meta & kDonated)) break;
+                        if (!(meta & kDonated)) {
+                            // (LDS) a level whose next value is over the budget is left too
+                            if (EXT && cfg.lds >= 0 && L.dab(t) >= cfg.lds) { ++cuts; continue; }
+                            break;
+                        }
                     }
                     if (!finished) {
                         u = L.u(t);
@@ -1141,7 +1156,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         if (onedir) dir = L.zi(t); else zi = L.zi(t);
                         y = L.y(t);
                         rhoP = L.rho(t);
-                        dab = L.dab(t);
+                        if (EXT) dab = L.dab(t);
                         Bt = Btab[t];
                         act = kNext;
                     }
@@ -1292,7 +1307,7 @@ int64_t walker_bytes(int Kmax, int dimPad) { return WalkerLayout{Kmax, dimPad}.b
 int64_t donation_slot_bytes(int Kmax, int dimPad) { return donation_stride(Kmax, dimPad); }
 
 cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
-                        int Kmax, int dimPad, bool bounded, cudaStream_t st) {
+                        int Kmax, int dimPad, bool extended, cudaStream_t st) {
     WalkerLayout W{Kmax, dimPad};
     const int cpl = pick_cpl(lanes, P.dimMax);
     const int smem = enum_smem_bytes(lanes, threads, Kmax);
@@ -1310,7 +1325,7 @@ cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int block
     }
 #define MSP_LAUNCH(g, c)                                                                              \
     if (lanes == g && cpl == c) {                                                                     \
-        if (bounded) MSP_LAUNCH1(g, c, true)                                                          \
+        if (extended) MSP_LAUNCH1(g, c, true)                                                         \
         else MSP_LAUNCH1(g, c, false)                                                                 \
     }
     MSP_ENUM_SHAPES(MSP_LAUNCH)
