@@ -146,14 +146,20 @@ __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ 
         const int j = lane + 32 * q;
         acc[q] = (j <= k) ? __ll2double_rn(Grow[j]) : 0.0;
     }
+    // column blocks q0 .. nq-1 hold the columns i < j <= k of a step: the
+    // others are skipped by warp-uniform branches (an FP64 warp instruction
+    // costs the same with no active lane as with 32)
+    const int nq = (k >> 5) + 1;
     for (int i = 0; i < k; ++i) {
         const double rki = __shfl_sync(kFull, pick4(acc, i >> 5), i & 31);
         const double muki = invB ? __dmul_rn(rki, invB[i]) : __ddiv_rn(rki, B[i]);
+        const int q0 = (i + 1) >> 5;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int j = lane + 32 * q;
-            if (j > i && j < k) acc[q] = __fma_rn(-mu_at(j, i), rki, acc[q]);
-            else if (j == k) acc[q] = __fma_rn(-muki, rki, acc[q]);
+            if (q >= q0 && q < nq) {
+                const int j = lane + 32 * q;
+                if (j > i && j <= k) acc[q] = __fma_rn(-(j < k ? mu_at(j, i) : muki), rki, acc[q]);
+            }
         }
         if (lane == 0) {
             if (rrow) rrow[i] = rki;
