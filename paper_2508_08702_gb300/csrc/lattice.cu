@@ -22,6 +22,54 @@ namespace msp {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int64_t kEntryLimit = (int64_t)1 << 58;   // |entries| < 2^58: 128-bit dots cannot overflow
 
+// Integer-pipe forms of FP64 steps of the block search (an FP64 instruction
+// costs ~64 cycles on GB300), each exact for every input it sees there:
+// int -> double for |v| < 2^31
+__device__ __forceinline__ double svp_i2d(int v) {
+    if (v == 0) return 0.0;
+    const unsigned a = v < 0 ? (unsigned)(-v) : (unsigned)v;
+    const int lz = __clz(a);
+    const unsigned long long m = ((unsigned long long)a << (lz + 21)) & 0x000fffffffffffffULL;
+    return __longlong_as_double((long long)(((unsigned long long)(v < 0) << 63) |
+                                            ((unsigned long long)(1023 + 31 - lz) << 52) | m));
+}
+
+// a < b for a >= +0 (or NaN) and b > 0: the unsigned order of the bit patterns
+// (a NaN compares not-less, as in FP64)
+__device__ __forceinline__ bool svp_less(double a, double b) {
+    return (unsigned long long)__double_as_longlong(a) < (unsigned long long)__double_as_longlong(b);
+}
+
+// c = -y rounded to nearest, ties to even (rint), and the side s = +1 if
+// c >= rint(c) else -1; returns true when |rint(c)| > 1e9
+__device__ __forceinline__ bool svp_round(double y, int& u1, int& s) {
+    const unsigned long long c = (unsigned long long)__double_as_longlong(y) ^ 0x8000000000000000ULL;
+    const bool neg = (c >> 63) != 0;
+    const int e = (int)((c >> 52) & 0x7ff);
+    const unsigned long long frac = c & 0x000fffffffffffffULL;
+    if (e >= 1023 + 30) return true;   // |c| >= 2^30 (or inf, NaN): |rint(c)| > 1e9
+    unsigned long long mag;
+    bool up, exact;
+    const int shift = 1075 - e;        // >= 22
+    if (e == 0 || shift > 63) {        // |c| < 2^-11: rounds to 0
+        mag = 0;
+        up = false;
+        exact = (e == 0 && frac == 0);
+    } else {
+        const unsigned long long m = frac | 0x0010000000000000ULL;
+        const unsigned long long ip = m >> shift;
+        const unsigned long long rem = m & ((1ULL << shift) - 1ULL);
+        const unsigned long long half = 1ULL << (shift - 1);
+        up = rem > half || (rem == half && (ip & 1ULL));
+        exact = rem == 0;
+        mag = ip + (up ? 1ULL : 0ULL);
+    }
+    if (mag > 1000000000ULL) return true;
+    u1 = neg ? -(int)mag : (int)mag;
+    s = neg ? ((up || exact) ? 1 : -1) : (up ? -1 : 1);
+    return false;
+}
+
 // Step a1: generator of Eq. (2) with bounds 0 <= x_j <= r_j: column 0 is
 // (-N d, -r_max (n times), r_max), column j is (N a_j, 2 c_j e_j, 0).
 __global__ void __launch_bounds__(128) build_lattice_kernel(Pools P, int64_t N) {
@@ -226,9 +274,27 @@ __device__ int32_t lll_warp(int64_t* __restrict__ b, int64_t* __restrict__ G, do
             if (pass > 1000) { st = ST_ECAP; break; }
             gso_row_warp(k, G + (int64_t)k * K, mu_at, B, nullptr, mu + k, K, &B[k], lane, invB);
             bool changed = false, ovf = false;
-            for (int j = k - 1; j >= 0; --j) {
-                const double mkj = mu[(int64_t)j * K + k];
-                if (fabs(mkj) > eta) {
+            // j = k-1 .. 0: the next j to reduce is the largest one at or
+            // below jtop whose current |mu_kj| exceeds eta -- found for 32
+            // columns at a time by a ballot (the values in between stay
+            // below eta: only a reduction at a larger j changes them)
+            const long long eta_bits = __double_as_longlong(eta);
+            for (int jtop = k - 1; jtop >= 0;) {
+                int j = -1;
+                for (int base = jtop & ~31; base >= 0; base -= 32) {
+                    const int jj = base + lane;
+                    bool big = false;
+                    if (jj <= jtop) {   // |mu| > eta on the bit pattern (no NaN passes, as in FP64)
+                        const long long ab = __double_as_longlong(mu[(int64_t)jj * K + k]) & 0x7fffffffffffffffLL;
+                        big = ab > eta_bits && ab <= 0x7ff0000000000000LL;
+                    }
+                    const unsigned bal = __ballot_sync(kFull, big);
+                    if (bal) { j = base + 31 - __clz(bal); break; }
+                }
+                if (j < 0) break;
+                jtop = j - 1;
+                {
+                    const double mkj = mu[(int64_t)j * K + k];
                     const double qd = rint(mkj);
                     if (fabs(qd) > 4503599627370496.0) { ovf = true; break; }
                     const int64_t q = (int64_t)qd;
@@ -544,13 +610,10 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
                         bool zp = true;
                         for (int i = t + 1; i < h; ++i) if (u[i] != 0) { zp = false; break; }
                         double acc = 0.0;
-                        for (int i = h - 1; i > t; --i) acc = __fma_rn((double)u[i], mu2[(int64_t)t * dd + i], acc);
+                        for (int i = h - 1; i > t; --i) acc = __fma_rn(svp_i2d(u[i]), mu2[(int64_t)t * dd + i], acc);
                         yv[t] = acc;
-                        const double cstar = -acc;
-                        const double r1 = rint(cstar);
-                        if (fabs(r1) > 1e9) { st = ST_EOVERFLOW; break; }
-                        int uu = (int)r1;
-                        const int sgn = (cstar >= r1) ? 1 : -1;
+                        int uu = 0, sgn = 1;   // rint(-acc) and its side
+                        if (svp_round(acc, uu, sgn)) { st = ST_EOVERFLOW; break; }
                         if (zp) uu = 0;
                         u1v[t] = uu;
                         ziv[t] = 1;
@@ -569,11 +632,11 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
                             cur = (zi % 2 == 0) ? u1v[t] + sgn * (zi / 2) : u1v[t] - sgn * ((zi - 1) / 2);
                         }
                     }
-                    const double x = __dadd_rn((double)cur, yv[t]);
-                    const double rho = __fma_rn(__dmul_rn(x, x), B2[t], rhoP[t]);
+                    const double x = __dadd_rn(svp_i2d(cur), yv[t]);
+                    const double rho = __fma_rn(__dmul_rn(x, x), B2[t], rhoP[t]);   // >= +0 (B_t > 0)
                     ++nloc;
                     if ((nloc & 4095) == 0 && global_time_ns() > deadline) { st = ST_ECAP; break; }
-                    if (!(rho < A)) {   // level exhausted: back to the parent
+                    if (!svp_less(rho, A)) {   // level exhausted: back to the parent
                         u[t] = 0;
                         if (t == h - 1) break;
                         ++t;
