@@ -197,21 +197,28 @@ __device__ __forceinline__ void gso_row_warp(int k, const int64_t* __restrict__ 
     // column blocks q0 .. nq-1 hold the columns i < j <= k of a step: the
     // others are skipped by warp-uniform branches (an FP64 warp instruction
     // costs the same with no active lane as with 32)
+    // (steps i of block qb broadcast from acc[qb]: the block index is a
+    // compile-time constant, so no select sits on the serial chain)
     const int nq = (k >> 5) + 1;
-    for (int i = 0; i < k; ++i) {
-        const double rki = __shfl_sync(kFull, pick4(acc, i >> 5), i & 31);
-        const double muki = invB ? __dmul_rn(rki, invB[i]) : __ddiv_rn(rki, B[i]);
-        const int q0 = (i + 1) >> 5;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (q >= q0 && q < nq) {
-                const int j = lane + 32 * q;
-                if (j > i && j <= k) acc[q] = __fma_rn(-(j < k ? mu_at(j, i) : muki), rki, acc[q]);
+    for (int qb = 0; qb < 4; ++qb) {
+        if (qb >= nq) break;
+        const int iend = min(k, 32 * qb + 32);
+        for (int i = 32 * qb; i < iend; ++i) {
+            const double rki = __shfl_sync(kFull, acc[qb], i & 31);
+            const double muki = invB ? __dmul_rn(rki, invB[i]) : __ddiv_rn(rki, B[i]);
+            const int q0 = (i + 1) >> 5;
+#pragma unroll
+            for (int q = qb; q < 4; ++q) {
+                if (q >= q0 && q < nq) {
+                    const int j = lane + 32 * q;
+                    if (j > i && j <= k) acc[q] = __fma_rn(-(j < k ? mu_at(j, i) : muki), rki, acc[q]);
+                }
             }
-        }
-        if (lane == 0) {
-            if (rrow) rrow[i] = rki;
-            murow[(int64_t)i * mstride] = muki;
+            if (lane == 0) {
+                if (rrow) rrow[i] = rki;
+                murow[(int64_t)i * mstride] = muki;
+            }
         }
     }
     const double rkk = __shfl_sync(kFull, pick4(acc, k >> 5), k & 31);
@@ -607,8 +614,8 @@ __global__ void __launch_bounds__(32) bkz_kernel(Pools P, BkzScratch S, int beta
                 for (;;) {
                     int cur;
                     if (enter) {
-                        bool zp = true;
-                        for (int i = t + 1; i < h; ++i) if (u[i] != 0) { zp = false; break; }
+                        // zero prefix above t: the parent's flag and its current value
+                        const bool zp = (t == h - 1) || ((flg[t + 1] & 1) && u[t + 1] == 0);
                         double acc = 0.0;
                         for (int i = h - 1; i > t; --i) acc = __fma_rn(svp_i2d(u[i]), mu2[(int64_t)t * dd + i], acc);
                         yv[t] = acc;
