@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--lanes", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--cpu-seconds", type=float, default=30.0)
     p.add_argument("--instances", type=int, default=64,
                    help="run only the first K instances of the batch (small profiling cases)")
     p.add_argument("--workload", default="batch64", choices=["batch64"] + sorted(WORKLOADS),
@@ -273,8 +273,50 @@ def oracle_nodes_per_s(instances, seconds: float):
 
 def cpu_sample(instances):
     """Bounded sample of the batch for the oracle: the instances with m <= 6
-    (the m = 7 instances take the oracle 3 to 70 s each)."""
+    (the m = 7 instances take the oracle 2 to 70 s each)."""
     return [x for x in instances if x.m <= 6]
+
+
+def cpu_baseline_sample(instances):
+    """The oracle baseline's sample (10 to 30 s of one core): the instances
+    with m <= 6 and the m = 7 ones with D >= 100 (2 to 7 s each; with D = 50
+    they take 30 to 70 s)."""
+    return [x for x in instances if x.m <= 6 or (x.m == 7 and getattr(x, "D", 0) >= 100)]
+
+
+def _oracle_solve_nodes(Ad):
+    """One instance through the oracle (a worker of the parallel leg)."""
+    from oracle import oracle as O
+    A, d = Ad
+    return O.solve(A, d).result.nodes
+
+
+def oracle_parallel_nodes_per_s(instances, workers: int):
+    """The oracle one instance per core (a spawned process pool: started
+    after GPU work, so no fork); returns (nodes/s, nodes, wall seconds)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_solve_nodes, [(instances[0].A, instances[0].d)] * workers)   # workers up
+        t0 = time.perf_counter()
+        nodes = sum(pool.map(_oracle_solve_nodes, [(x.A, x.d) for x in instances], chunksize=1))
+        dt = time.perf_counter() - t0
+    return nodes / dt, nodes, dt
+
+
+def host_cpu():
+    """Core count and model of the host, as lscpu reports them."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "model": model or platform.processor(), "machine": platform.machine()}
 
 
 def reference_arm(args, rank, world):
@@ -440,10 +482,19 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, nodes, dt, cnt = oracle_nodes_per_s(cpu_sample(insts), args.cpu_seconds)
+        sample = cpu_baseline_sample(insts)
+        v, nodes, dt, cnt = oracle_nodes_per_s(sample, args.cpu_seconds)
+        host = host_cpu()
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {cnt} batch instances with m<=6 ({nodes} nodes, {dt:.1f} s), "
-                                          f"LLL + enumeration, one thread"}
+                                "sample": f"first {cnt} of the {len(sample)} batch instances with m<=6 or "
+                                          f"(m=7, D>=100) ({nodes} nodes, {dt:.1f} s), LLL + enumeration, "
+                                          f"one thread",
+                                "host": host}
+        if host["nproc"] and host["nproc"] > 1:
+            pv, pn, pdt = oracle_parallel_nodes_per_s(sample[:cnt], host["nproc"])
+            line["cpu_baseline"]["parallel"] = {
+                "value": pv, "unit": UNIT, "cores": host["nproc"],
+                "sample": f"the same {cnt} instances, one instance per core ({pn} nodes, {pdt:.1f} s wall)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
