@@ -66,6 +66,8 @@ WORKLOADS = {
     "m9_all": ("m9_n80", "all", 1200.0),    # m=9, n=80, D=100, 8 instances, 40 ones planted
     "m8_first": ("m8_n70", "first", 120.0),
     "m12_first": ("m12_n110", "first", 60.0),   # m=12, n=110, D=100, 4 instances
+    "m10d50_first": ("m10_n90_d50", "first", 30.0),    # m=10, n=90, D=50, 4 instances
+    "m11d50_first": ("m11_n100_d50", "first", 30.0),   # m=11, n=100, D=50, 4 instances
     "m12d50_first": ("m12_n110_d50", "first", 60.0),   # m=12, n=110, D=50 (the paper's m=12 row), 4 instances
     "cd8_all": ("cd8", "all", 600.0),       # Cornuejols-Dawande m=8 (nothing planted), 16 instances
 }

@@ -107,6 +107,18 @@ def m12_n110_d50(count: int = 4) -> List[Instance]:
     return [make_instance(5100 + i, 12, 110, 50, tag=f"m12d50_{i}") for i in range(count)]
 
 
+def m10_n90_d50(count: int = 4) -> List[Instance]:
+    """m=10, n=90, D=50, seeds 5200.. (planted Bernoulli(1/2)): the shape of
+    the paper's (10, 90, 50) row."""
+    return [make_instance(5200 + i, 10, 90, 50, tag=f"m10d50_{i}") for i in range(count)]
+
+
+def m11_n100_d50(count: int = 4) -> List[Instance]:
+    """m=11, n=100, D=50, seeds 5300.. (planted Bernoulli(1/2)): the shape of
+    the paper's (11, 100, 50) row."""
+    return [make_instance(5300 + i, 11, 100, 50, tag=f"m11d50_{i}") for i in range(count)]
+
+
 def training_set(count: int = 256, first_seed: int = 30000) -> List[Instance]:
     """Training instances for the subtree scorer: m cycling 5,6,7, D cycling
     over {50, 100, 200}; seeds disjoint from every evaluation set."""
