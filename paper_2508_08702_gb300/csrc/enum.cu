@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     int inst = 0, dd = 0, dim = 0, sx = 0, Sf = 0, t0 = 0, t = 0;
     long long Rbits = 0, eps_fix = 0;
     int ehalf = 0;
-    long long rmax = 1;   // stays the constant 1 in the binary variant
+    long long rmax = 1;   // stays the constant 1 in the plain variant
     double eps = 0.0;
     const double* muT = nullptr;
     const double* Btab = nullptr;
