@@ -66,14 +66,21 @@
  *   R11 Instances are made feasible by a planted binary x, d = A x (the
  *       construction of the paper's instance library is not described).
  *   R12 Limited discrepancy search (Sec. 3, after Harvey and Ginsberg): a
- *       discrepancy is a level where u_t differs from the heuristic first
- *       value u^1 of that level's walk (the rounded centre; 0 on the
- *       all-zero levels of sym mode), whatever its rank in the zig-zag.
- *       Iteration k walks Algorithm 1 but tries a value other than u^1 only
- *       while the path above carries fewer than k discrepancies, and reports
- *       a leaf only when its path carries exactly k, so iterations
- *       k = 0, 1, 2, ... report every solution exactly once.  Nodes are
- *       counted as in R8 (the nodes of lower discrepancy are visited again).
+ *       discrepancy is a deviation from the heuristic order of a level's
+ *       walk, whose first value u^1 is the rounded centre (0 on the all-zero
+ *       levels of sym mode).  The paper does not say what a deviation to a
+ *       later value of a many-valued level costs; two readings:
+ *         rank (lds_rank = 1, the default): the value at position p of the
+ *           level's walk (p = 0 for u^1, counting every value the walk
+ *           takes, the one-direction phase after a Hoelder failure
+ *           included) costs p discrepancies;
+ *         flat (lds_rank = 0): every value other than u^1 costs one.
+ *       The cost of a path is the sum over its levels.  Iteration k walks
+ *       Algorithm 1 but tries a value only while the path's cost stays at
+ *       most k, and reports a leaf only when the cost is exactly k, so
+ *       iterations k = 0, 1, 2, ... report every solution exactly once.
+ *       Nodes are counted as in R8 (the nodes of lower cost are visited
+ *       again).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (see oracle/build.py).
  */
@@ -375,6 +382,9 @@ typedef struct {
                         /* values u[sub_level+1 .. dd-1] are given; -1: off       */
     int lds;            /* >= 0: one limited-discrepancy iteration with this     */
                         /* budget (R12); -1: plain depth-first search            */
+    int lds_rank;       /* 1: a value's discrepancy is its position in its       */
+                        /* level's walk (the k-th value tried costs k-1); 0:     */
+                        /* every value after the first costs one (R12)           */
 } oracle_enum_opts;
 
 typedef struct {
@@ -460,11 +470,19 @@ static int leaf_check(enum_state *e)
     return 1;
 }
 
+/* Discrepancy of the value at position pos (0-based) of a level's walk,
+ * u the value and u1 the first one (R12). */
+static int value_cost(const enum_state *e, long pos, long u, long u1)
+{
+    return e->o.lds_rank ? (int)pos : (u != u1);
+}
+
 /* enum(t, w') of Algorithm 1.  wp = w^{(t+1)}, rho_p = ||w^{(t+1)}||^2. */
 static void enum_level(enum_state *e, int t, const double *wp, double rho_p, int disc)
 {
     const int dd = e->dd, dim = e->dim;
     double w[dim];
+    long pos = 0;                                  /* position of u in this level's walk */
 
     int zero_prefix = 1;
     for (int i = t + 1; i < dd; ++i) if (e->u[i] != 0) { zero_prefix = 0; break; }
@@ -480,7 +498,8 @@ static void enum_level(enum_state *e, int t, const double *wp, double rho_p, int
     long u = u1;
 
     for (;;) {
-        if (e->o.lds >= 0 && u != u1 && disc + 1 > e->o.lds) {   /* budget spent (R12) */
+        const int cost = value_cost(e, pos, u, u1);
+        if (e->o.lds >= 0 && cost > 0 && disc + cost > e->o.lds) {   /* budget spent (R12) */
             e->s.lds_cuts++;
             return;
         }
@@ -504,6 +523,7 @@ static void enum_level(enum_state *e, int t, const double *wp, double rho_p, int
                 u = zigzag(u1, s, zi);
                 dir = (u > u1) ? 1 : -1;
                 onedirection = 1;
+                pos += 1;
                 continue;
             }
             if (!fail) {
@@ -515,13 +535,13 @@ static void enum_level(enum_state *e, int t, const double *wp, double rho_p, int
                         e->pre_rho[p] = rho;
                     }
                 } else {
-                    enum_level(e, t - 1, w, rho, disc + (u != u1));  /* step forward */
+                    enum_level(e, t - 1, w, rho, disc + cost);  /* step forward */
                     if (e->s.stopped) return;
                 }
             }
         } else {
             e->s.leaves++;
-            if ((e->o.lds < 0 || disc + (u != u1) == e->o.lds) && leaf_check(e)) {
+            if ((e->o.lds < 0 || disc + cost == e->o.lds) && leaf_check(e)) {
                 int64_t q = e->s.nsol++;
                 if (q < e->sol_cap) memcpy(e->sol + (size_t)q * e->n, e->xbuf, (size_t)e->n);
                 if (e->o.first) { e->s.stopped = 1; return; }
@@ -529,6 +549,47 @@ static void enum_level(enum_state *e, int t, const double *wp, double rho_p, int
         }
         if (onedirection) u += dir;                 /* next(u_t) */
         else { zi += 1; u = zigzag(u1, s, zi); }
+        pos += 1;
+    }
+}
+
+/* Position of the value target in the walk of level t (the same sequence of
+ * values and tests enum_level takes, without descending), given the centre
+ * y, w^{(t+1)} and its norm; -1 if the walk never reaches it. */
+static long level_position(const enum_state *e, int t, double y, const double *wp, double rho_p,
+                           int zero_prefix, long target)
+{
+    const int dim = e->dim;
+    double w[dim];
+    const double cstar = -y;
+    long u1 = (long)rint(cstar);
+    const int s = (cstar >= (double)u1) ? 1 : -1;
+    int onedirection = 0;
+    long dir = 0, zi = 1, pos = 0;
+    if (zero_prefix && e->o.sym) { u1 = 0; onedirection = 1; dir = 1; }
+    long u = u1;
+    for (;;) {
+        if (u == target) return pos;
+        const double x = (double)u + y;
+        const double xx = x * x;
+        const double rho = fma(xx, e->B[t], rho_p);
+        if (rho > e->Rb) return -1;
+        if (t > 0 && e->o.hoelder == HOELDER_CUT) {
+            for (int c = 0; c < dim; ++c) w[c] = fma(x, e->bhat[(size_t)t * dim + c], wp[c]);
+            const double h = (double)e->rmax * norm1(w, dim, e->o.lanes) + e->eps;
+            if (rho > h) {
+                if (onedirection) return -1;
+                zi += 1;
+                u = zigzag(u1, s, zi);
+                dir = (u > u1) ? 1 : -1;
+                onedirection = 1;
+                pos += 1;
+                continue;
+            }
+        }
+        if (onedirection) u += dir;
+        else { zi += 1; u = zigzag(u1, s, zi); }
+        pos += 1;
     }
 }
 
@@ -576,7 +637,13 @@ int oracle_enumerate_bounds(int dd, int dim, const double *mu, const double *B, 
             e.u[t] = prefix_u[t];
             const double y = center(&e, t);
             const long first = (zero_prefix && o->sym) ? 0 : (long)rint(-y);   /* u^1 of level t */
-            disc0 += (e.u[t] != first);
+            if (o->lds >= 0 && o->lds_rank) {
+                const long p = level_position(&e, t, y, w0, rho0, zero_prefix, e.u[t]);
+                if (p < 0) { free(e.u); free(e.vbuf); free(e.xbuf); free(w0); return OR_EINVAL; }
+                disc0 += (int)p;
+            } else {
+                disc0 += (e.u[t] != first);
+            }
             zero_prefix = zero_prefix && (e.u[t] == 0);
             const double x = (double)e.u[t] + y;
             const double xx = x * x;

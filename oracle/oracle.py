@@ -33,7 +33,7 @@ class OracleError(RuntimeError):
 class _EnumOpts(C.Structure):
     _fields_ = [("hoelder", C.c_int), ("sym", C.c_int), ("lanes", C.c_int),
                 ("use_eps", C.c_int), ("first", C.c_int), ("split_level", C.c_int),
-                ("sub_level", C.c_int), ("lds", C.c_int)]
+                ("sub_level", C.c_int), ("lds", C.c_int), ("lds_rank", C.c_int)]
 
 
 class _EnumStats(C.Structure):
@@ -202,17 +202,19 @@ def enumerate(kern: np.ndarray, g: GSO, A: np.ndarray, d: np.ndarray, *,
               hoelder: int = HOELDER_CUT, sym: bool = True, lanes: int = 32,
               use_eps: bool = True, first: bool = False,
               split_level: int = -1, sub_level: int = -1,
-              prefix: Optional[np.ndarray] = None, lds: int = -1, r=None,
+              prefix: Optional[np.ndarray] = None, lds: int = -1, lds_rank: bool = True, r=None,
               sol_cap: int = 1 << 16, prefix_cap: int = 1 << 20) -> EnumResult:
     """Algorithm 1 over the whole tree, the top part down to ``split_level``
     (recording prefixes), or the subtree below ``prefix`` at ``sub_level``.
-    ``lds`` >= 0 runs one limited-discrepancy iteration with that budget."""
+    ``lds`` >= 0 runs one limited-discrepancy iteration with that budget;
+    ``lds_rank`` picks the discrepancy cost of a value (its position in the
+    level's walk, else one for every value after the first; R12)."""
     kb = np.ascontiguousarray(kern, dtype=np.int32)
     A = np.ascontiguousarray(A, dtype=np.int32)
     d = np.ascontiguousarray(d, dtype=np.int64)
     dd, dim = kb.shape
     m, n = A.shape
-    o = _EnumOpts(hoelder, int(sym), lanes, int(use_eps), int(first), split_level, sub_level, lds)
+    o = _EnumOpts(hoelder, int(sym), lanes, int(use_eps), int(first), split_level, sub_level, lds, int(lds_rank))
     pu = np.ascontiguousarray(prefix if prefix is not None else np.zeros(dd), dtype=np.int32)
     sol = np.zeros((sol_cap, max(n, 1)), np.uint8)
     pcap = prefix_cap if split_level >= 0 else 0
