@@ -51,7 +51,7 @@ typedef enum {
     MSP_ETIMEOUT = 6,    /* time cap reached; results are partial                */
     MSP_ETRUNC = 7,      /* solution buffer too small; counts stay exact         */
     MSP_ESTATE = 8,      /* call order violated                                  */
-    MSP_ECAP = 9,        /* LLL iteration cap reached                            */
+    MSP_ECAP = 9,        /* LLL iteration cap, or opts.lds_max, reached          */
     MSP_EQUEUE = 10      /* work queue capacity exceeded                         */
 } msp_status;
 
@@ -99,8 +99,11 @@ typedef struct {
     int log_features;      /* [0] 1: compute the 32 features of every subtree prefix      */
                            /*     (msp_export_features), e.g. to train the scorer         */
     int lds_budget;        /* [-1] MSP_LDS: >= 0 runs only the iteration with this budget */
-    int lds_max;           /* [127] MSP_LDS: last budget tried (at most 127; 127 always   */
-                           /*       exhausts a tree, whose paths have at most 127 levels) */
+                           /*      (at most 255)                                          */
+    int lds_max;           /* [127] MSP_LDS: last budget tried (at most 255); an instance */
+                           /*       not finished by then reports MSP_ECAP.  With          */
+                           /*       lds_rank = 0 the budget 127 always exhausts a tree    */
+                           /*       (its paths have at most 127 levels)                   */
     int first_split_target; /* [16384] split target of MSP_FIRST when split_target = 0: */
                            /*       small subtrees let a good queue order pay off        */
     int bkz_beta;          /* [0] >= 2: BKZ-beta of the kernel basis after LLL (Sec. 2   */
@@ -117,6 +120,10 @@ typedef struct {
                            /*     its columns by Fisher-Yates (j = n-1 .. 1, swap j with */
                            /*     z mod (j+1)) fed by splitmix64 from                    */
                            /*     replica_seed ^ (i << 32) ^ k; replica 0 is unshuffled  */
+    int lds_rank;          /* [1] MSP_LDS: discrepancy cost of a value -- 1: its position */
+                           /*     p in its level's walk (p = 0 for the rounded centre),  */
+                           /*     0: one for every value after the first (Sec. 3 calls  */
+                           /*     a discrepancy a deviation from the heuristic order)    */
 } msp_opts;
 
 /* Per-instance results of an enumeration. */

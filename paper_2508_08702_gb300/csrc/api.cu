@@ -296,6 +296,7 @@ void msp_default_opts(msp_opts* o) {
     o->log_features = 0;
     o->lds_budget = -1;
     o->lds_max = 127;
+    o->lds_rank = 1;
     o->first_split_target = 16384;
     o->bkz_beta = 0;
     o->bkz_max_tours = 16;
@@ -314,7 +315,7 @@ const char* msp_status_string(int s) {
         case MSP_ETIMEOUT: return "time cap reached";
         case MSP_ETRUNC: return "solution buffer too small";
         case MSP_ESTATE: return "call order violated";
-        case MSP_ECAP: return "LLL iteration cap reached";
+        case MSP_ECAP: return "iteration cap reached (LLL, or the last budget of the discrepancy search)";
         case MSP_EQUEUE: return "work queue capacity exceeded";
         default: return "unknown status";
     }
@@ -335,7 +336,7 @@ msp_status msp_create(msp_ctx** out, const msp_opts* opts, void* stream) {
         o.hoelder < 0 || o.hoelder > 2 || (o.lanes != 0 && o.lanes != 4 && o.lanes != 8 && o.lanes != 16 && o.lanes != 32) ||
         o.split_depth < 0 || o.warps_per_block < 1 || o.warps_per_block > 8 || o.sol_capacity < 1 ||
         o.lll_max_iter < 1 || !(o.max_seconds > 0.0) || o.donation_capacity < 0 || o.lds_budget < -1 ||
-        o.lds_budget > 127 || o.lds_max < 0 || o.lds_max > 127 || o.first_split_target < 0 ||
+        o.lds_budget > 255 || o.lds_max < 0 || o.lds_max > 255 || (o.lds_rank != 0 && o.lds_rank != 1) || o.first_split_target < 0 ||
         o.bkz_beta < 0 || o.bkz_beta == 1 || o.bkz_beta > 128 || o.bkz_max_tours < 1 || o.replicas < 1 ||
         o.replicas > 64) {
         delete c;
@@ -590,7 +591,7 @@ msp_status msp_reduce(msp_ctx* c) {
 // solutions, start time and deadline carry over).
 static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_cap_s, int lds = -1,
                                   bool cont = false) {
-    EnumCfg cfg{c->o.hoelder, c->o.sym, c->o.use_eps, mode == MSP_FIRST ? 1 : 0, lds};
+    EnumCfg cfg{c->o.hoelder, c->o.sym, c->o.use_eps, mode == MSP_FIRST ? 1 : 0, lds, c->o.lds_rank};
     int blocks, threads;
     enum_launch_shape(c, &blocks, &threads);
     const int64_t walkers = walkers_of(c, blocks, threads);
@@ -883,6 +884,8 @@ msp_status msp_wait(msp_ctx* c, msp_stats* stats, msp_stats* total) {
         S.lds_budget = (c->last_lds && i < (int)c->lds_done.size()) ? c->lds_done[i] : -1;
         int32_t st = h[i].status;
         if (st == MSP_OK && ctl.stop == 2) st = MSP_ETIMEOUT;
+        // the iterated discrepancy search reached opts.lds_max with the tree not exhausted
+        if (st == MSP_OK && c->last_lds && c->o.lds_budget < 0 && S.lds_budget < 0) st = MSP_ECAP;
         if (st == MSP_OK && trunc) st = MSP_ETRUNC;
         S.status = st;
         S.ms = ms;

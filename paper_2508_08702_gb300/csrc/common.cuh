@@ -84,7 +84,7 @@ struct Pools {
     int32_t* fu;
     double* frho;
     double* fw;
-    int32_t* fdisc;                    // per prefix: levels where u differs from the first zig-zag value
+    int32_t* fdisc;                    // per prefix: discrepancy cost of the path (limited discrepancy search)
     float* fxsum;                      // per prefix: sum over its levels of |x|
     int64_t F;
     // work queue
@@ -153,6 +153,7 @@ struct EnumCfg {
     int use_eps;     // slack eps = (n+1) 2^-20 on both tests
     int first;       // stop at the first solution
     int lds;         // >= 0: one limited-discrepancy iteration with this budget; -1: depth-first
+    int lds_rank;    // discrepancy cost of a value: 1 its position in the level's walk, 0 one if not the first
 };
 
 __device__ __forceinline__ int64_t frontier_index(const Pools& P, int inst, int sel, int64_t j) {

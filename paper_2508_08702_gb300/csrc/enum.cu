@@ -21,9 +21,10 @@
 //   norm failure: step back.
 //   t = 0: exact integer check of v = sum_j u_j b_j (Theorem 1).
 // Limited discrepancy search (Sec. 3): a value other than the first of its
-// level's walk (u^1, the rounded centre) is a discrepancy; an iteration with
-// budget k tries such a value only while the path above carries fewer than
-// k of them and reports a leaf only when its path carries exactly k.
+// level's walk (u^1, the rounded centre) is a discrepancy, costing its
+// position p in the walk (rank reading) or one (flat reading); an iteration
+// with budget k tries a value only while the path's cost stays at most k and
+// reports a leaf only when the cost is exactly k.
 // The centre uses the partial-sum cache of Gama-Nguyen-Regev: sigma[t][i]
 // holds the fold down to index i, J[t] the highest level changed since, so
 // only the changed tail of the fold is redone -- the same operations in
@@ -83,9 +84,11 @@ __device__ int64_t expand_parent(const Pools& P, const EnumCfg& cfg, int inst, i
     int dir = 0, zi = 1;
     if (zp && cfg.sym) { u1 = 0; onedir = true; dir = 1; }
     int u = u1;
+    int pos = 0;   // position of u in this level's walk
     int64_t nch = 0;
     for (;;) {
-        if (cfg.lds >= 0 && u != u1 && pdisc >= cfg.lds) {   // discrepancy budget spent
+        const int cost = cfg.lds_rank ? pos : (u != u1 ? 1 : 0);
+        if (cfg.lds >= 0 && cost > 0 && pdisc + cost > cfg.lds) {   // discrepancy budget spent
             if (WRITE) ++cuts;
             break;
         }
@@ -118,6 +121,7 @@ __device__ int64_t expand_parent(const Pools& P, const EnumCfg& cfg, int inst, i
             u = zigzag(u1, s, zi);
             dir = (u > u1) ? 1 : -1;
             onedir = true;
+            ++pos;
             continue;
         }
         if (!fail) {
@@ -127,7 +131,7 @@ __device__ int64_t expand_parent(const Pools& P, const EnumCfg& cfg, int inst, i
                 for (int i = 0; i < P.Kmax; ++i) ou[i] = (i > t && i < dd) ? pu[i] : 0;
                 ou[t] = u;
                 P.frho[o] = rho;
-                P.fdisc[o] = pdisc + (u != u1 ? 1 : 0);
+                P.fdisc[o] = pdisc + cost;
                 P.fxsum[o] = pxsum + (float)fabs(x);
                 double* ow = P.fw + o * P.dimPad;
                 for (int c = 0; c < dim; ++c) ow[c] = __fma_rn(x, bhat[(int64_t)t * dim + c], pw[c]);
@@ -136,6 +140,7 @@ __device__ int64_t expand_parent(const Pools& P, const EnumCfg& cfg, int inst, i
         }
         if (onedir) u += dir;
         else { ++zi; u = zigzag(u1, s, zi); }
+        ++pos;
     }
     return nch;
 }
@@ -288,8 +293,8 @@ struct WalkerLayout {
 // Level state of one walker in shared memory: for each level t on the
 // current path, the value u being explored there (also as a double), the
 // zig-zag state, the quantised x, the centre y_t, the parent's norm
-// rho_{t+1} and the discrepancies above.  One base pointer; the arrays
-// follow each other.
+// rho_{t+1}, the discrepancy cost above and the position of u in the level's
+// walk.  One base pointer; the arrays follow each other.
 struct Levels {
     unsigned char* base;
     int K;
@@ -302,13 +307,15 @@ struct Levels {
     __device__ __forceinline__ short& zi(int t) const { return reinterpret_cast<short*>(base + 32 * K)[t]; }
     __device__ __forceinline__ unsigned char& meta(int t) const { return base[34 * K + t]; }
     __device__ __forceinline__ unsigned char& J(int t) const { return base[35 * K + t]; }
-    // discrepancies on the path above level t (limited discrepancy search)
+    // discrepancy cost of the path above level t (limited discrepancy search)
     __device__ __forceinline__ unsigned char& dab(int t) const { return base[36 * K + t]; }
+    // position of u(t) in the walk of level t (rank reading; at most the budget)
+    __device__ __forceinline__ unsigned char& pos(int t) const { return base[37 * K + t]; }
     // the queue item (prefix) of the current walk
-    __device__ __forceinline__ int64_t& gid() const { return *reinterpret_cast<int64_t*>(base + (37 * K + 7) / 8 * 8); }
+    __device__ __forceinline__ int64_t& gid() const { return *reinterpret_cast<int64_t*>(base + (38 * K + 7) / 8 * 8); }
 };
 
-__host__ __device__ inline int level_bytes(int Kmax) { return ((37 * Kmax + 7) / 8 * 8 + 8 + 15) / 16 * 16; }
+__host__ __device__ inline int level_bytes(int Kmax) { return ((38 * Kmax + 7) / 8 * 8 + 8 + 15) / 16 * 16; }
 
 __device__ __forceinline__ Levels levels_at(unsigned char* base, int Kmax) {
     Levels L;
@@ -322,7 +329,7 @@ __device__ __forceinline__ Levels levels_at(unsigned char* base, int Kmax) {
 // slot continues with int32 u[Kmax] (values above t) and the canonical FP64
 // w^(t+1) (double[dimPad]).
 struct DonHdr {
-    int32_t inst, t, u, u1, zi, meta, dab, pad;
+    int32_t inst, t, u, u1, zi, meta, dab, pos;
     int64_t gid;
     double y, rhoP;
 };
@@ -634,12 +641,15 @@ __device__ __noinline__ double canonical_l1(const double* __restrict__ bhat, con
 template <int G>
 __device__ __noinline__ int donate(const Pools& P, int inst, int64_t gid, const Levels& L, const double* root_w,
                                    const double* __restrict__ bhat, int t0, int t, int dd, int dim, int Kmax,
-                                   int lds, unsigned gmask) {
+                                   int lds, int lds_rank, unsigned gmask) {
     const int lg = threadIdx.x & (G - 1);
     if (P.don_cap <= 0) return 0;
     int h = -1;
     for (int l = t0; l > t; --l)   // untried values of a level are discrepancies: they need budget
-        if (!(L.meta(l) & kDonated) && (lds < 0 || L.dab(l) < lds)) { h = l; break; }
+        if (!(L.meta(l) & kDonated) && (lds < 0 || L.dab(l) + (lds_rank ? L.pos(l) + 1 : 1) <= lds)) {
+            h = l;
+            break;
+        }
     if (h < 0) return 0;
     // reserve ring index k (slot k mod cap); the slot is free once its
     // sequence number equals k (set by the consumer of index k - cap)
@@ -664,7 +674,7 @@ __device__ __noinline__ int donate(const Pools& P, int inst, int64_t gid, const 
         DonHdr hd;
         hd.inst = inst; hd.t = h; hd.u = L.u(h); hd.u1 = L.u1(h);
         hd.zi = L.zi(h); hd.meta = L.meta(h) & ~kDonated; hd.gid = gid;
-        hd.dab = L.dab(h); hd.pad = 0;
+        hd.dab = L.dab(h); hd.pos = L.pos(h);
         hd.y = L.y(h); hd.rhoP = L.rho(h);
         *reinterpret_cast<DonHdr*>(sp) = hd;
     }
@@ -752,7 +762,8 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     const int64_t* nbqtab = nullptr;
     double y = 0.0, rhoP = 0.0, Bt = 0.0;
     int u = 0, u1 = 0, s = 1, zi = 1, dir = 0, act = kEval;
-    int dab = 0;                       // discrepancies on the path above level t
+    int dab = 0;                       // discrepancy cost of the path above level t
+    int pos = 0;                       // position of u in the walk of level t
     bool onedir = false, zp = true;
     long long Epar = 0, nbq_t = 0;
     long long W[CPL];
@@ -914,7 +925,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     s = (hd.meta & kNegS) ? -1 : 1;
                     zp = (hd.meta & kZeroPrefix) != 0;
                     if (onedir) dir = hd.zi; else zi = hd.zi;
-                    if (EXT) dab = hd.dab;
+                    if (EXT) { dab = hd.dab; pos = hd.pos; }
                 }
                 for (int i = lg; i <= t0; i += G) L.J(i) = (unsigned char)(dd - 1);
                 if (lg == 0) L.meta(t0) = 0;
@@ -965,9 +976,11 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 onedir = false; dir = 0; zi = 1;
                 if (zp && cfg.sym) { u1 = 0; onedir = true; dir = 1; }
                 u = u1;
+                if (EXT) pos = 0;
             } else if (act == kNext) {
                 if (onedir) u += dir;
                 else { ++zi; u = zigzag(u1, s, zi); }
+                if (EXT) ++pos;
                 if (lg == 0 && t > 0 && L.J(t - 1) < t) L.J(t - 1) = (unsigned char)t;
             }
             __syncwarp(gmask);
@@ -993,8 +1006,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 else if (__shfl_sync(gmask, solved, 0, G)) { abort = true; quiet = true; }
                 else if (__shfl_sync(gmask, want, 0, G))
                     donate<G>(P, inst, L.gid(), L, root_w, P.bhat + P.inst[inst].offBhat, t0, t, dd, dim, Kmax,
-                              EXT ? cfg.lds : -1,
-                              gmask);
+                              EXT ? cfg.lds : -1, cfg.lds_rank, gmask);
                 // the 32-bit walk counters are flushed long before they could wrap
                 // (at most 1024 nodes and 1024 x 128 centre fmas between checks)
                 if (nodes >= (1u << 30) || cfma >= (1u << 30)) {
@@ -1021,7 +1033,9 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 // ---- node (t, u): centre, norm (FP64, the canonical operations) ----
                 const double x = __dadd_rn(i2d_exact(u), y);
                 const double rho = __fma_rn(__dmul_rn(x, x), Bt, rhoP);
-                const bool over_budget = EXT && cfg.lds >= 0 && u != u1 && dab >= cfg.lds;
+                // discrepancy cost of this value (limited discrepancy search)
+                const int cost = EXT ? (cfg.lds_rank ? pos : (u != u1 ? 1 : 0)) : 0;
+                const bool over_budget = EXT && cfg.lds >= 0 && cost > 0 && dab + cost > cfg.lds;
                 nodes += over_budget ? 0 : 1;
                 cuts += over_budget ? 1 : 0;
                 long long Ech = 0;
@@ -1032,7 +1046,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     ++passed;
                     if (t == 0) {
                         ++leaves;
-                        if (!EXT || cfg.lds < 0 || dab + (u != u1 ? 1 : 0) == cfg.lds)
+                        if (!EXT || cfg.lds < 0 || dab + cost == cfg.lds)
                             item_sols += EXT ? leaf_check_bounded<G, CPL>(P, cfg, inst, L, u, gmask)
                                              : leaf_check<G, CPL>(P, cfg, inst, L, u, gmask);
                         act = kNext;
@@ -1076,6 +1090,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                                 u = zigzag(u1, s, zi);
                                 dir = (u > u1) ? 1 : -1;
                                 onedir = true;
+                                if (EXT) ++pos;
                                 if (lg == 0 && L.J(t - 1) < t) L.J(t - 1) = (unsigned char)t;
                                 act = kEval;
                             }
@@ -1084,11 +1099,13 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         }
                     }
                 }
-                // limited discrepancy search: once the path above has spent the
-                // budget, every further value of this level is over it -- leave
-                // the level now (one cut, as when the value is tried) instead of
-                // spending a step on it
-                if (EXT && cfg.lds >= 0 && (act == kNext || act == kEval) && dab >= cfg.lds) {
+                // limited discrepancy search: once the next value of this level
+                // is over the budget, so is every later one (the cost does not
+                // fall along the walk) -- leave the level now (one cut, as when
+                // the value is tried) instead of spending a step on it.  After a
+                // kEval the next value is the one already set (position pos).
+                if (EXT && cfg.lds >= 0 && (act == kNext || act == kEval) &&
+                    dab + (cfg.lds_rank ? pos + (act == kNext ? 1 : 0) : 1) > cfg.lds) {
                     ++cuts;
                     act = kUp;
                 }
@@ -1103,9 +1120,12 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         L.xq(t) = xq;
                         L.y(t) = y;
                         L.rho(t) = rhoP;
-                        if (EXT) L.dab(t) = (unsigned char)dab;
+                        if (EXT) {
+                            L.dab(t) = (unsigned char)dab;
+                            L.pos(t) = (unsigned char)min(pos, 255);
+                        }
                     }
-                    if (EXT) dab += (u != u1) ? 1 : 0;
+                    if (EXT) dab += cost;
 #pragma unroll
                     {
                         // the child's W = W + xq Bq, recomputed instead of keeping the
@@ -1143,7 +1163,11 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         Epar -= (((long long)ehalf * (axt + 1)) >> 1) + nbq_t + 1;
                         if (!(meta & kDonated)) {
                             // (LDS) a level whose next value is over the budget is left too
-                            if (EXT && cfg.lds >= 0 && L.dab(t) >= cfg.lds) { ++cuts; continue; }
+                            if (EXT && cfg.lds >= 0 &&
+                                L.dab(t) + (cfg.lds_rank ? L.pos(t) + 1 : 1) > cfg.lds) {
+                                ++cuts;
+                                continue;
+                            }
                             break;
                         }
                     }
@@ -1156,7 +1180,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         if (onedir) dir = L.zi(t); else zi = L.zi(t);
                         y = L.y(t);
                         rhoP = L.rho(t);
-                        if (EXT) dab = L.dab(t);
+                        if (EXT) { dab = L.dab(t); pos = L.pos(t); }
                         Bt = Btab[t];
                         act = kNext;
                     }

@@ -42,42 +42,61 @@ def _oracle(inst, **kw):
     return O.enumerate(kern, g, inst.A, inst.d, lanes=8, **kw)
 
 
+@pytest.mark.parametrize("rank", [0, 1], ids=["flat", "rank"])
 @pytest.mark.parametrize("k", [0, 1, 3, 6])
 @pytest.mark.parametrize("depth", [0, 8, 24])
-def test_one_iteration_equals_oracle(k, depth):
+def test_one_iteration_equals_oracle(k, depth, rank):
     insts = MIXED if depth else SMALL   # one walker per instance without a split
     res, sols, ctx = M().solve(insts, order=M().MSP_LDS, lds_budget=k, split_depth=depth, lanes=8,
-                               max_seconds=120.0)
+                               max_seconds=120.0, lds_rank=rank)
     for i, inst in enumerate(insts):
-        ref = _oracle(inst, lds=k)
+        ref = _oracle(inst, lds=k, lds_rank=bool(rank))
         st = res.stats[i]
         assert (st["nodes"], st["passed"], st["leaves"]) == (ref.nodes, ref.passed, ref.leaves), (i, k)
         assert np.array_equal(sols[i], ref.solutions), (i, k)
     ctx.close()
 
 
-def test_iterated_all_mode_reports_every_solution_once():
-    res, sols, ctx = M().solve(SMALL, order=M().MSP_LDS, lanes=8, max_seconds=120.0)
+@pytest.mark.parametrize("rank", [0, 1], ids=["flat", "rank"])
+def test_iterated_all_mode_reports_every_solution_once(rank):
+    res, sols, ctx = M().solve(SMALL, order=M().MSP_LDS, lanes=8, max_seconds=120.0, lds_rank=rank)
     for i, inst in enumerate(SMALL):
         assert np.array_equal(sols[i], DEF.brute_force(inst.A, inst.d)), i
         _, kern, g = O.reduce(inst.A, inst.d)
-        its = O.enumerate_lds(kern, g, inst.A, inst.d, lanes=8)
+        its = O.enumerate_lds(kern, g, inst.A, inst.d, lanes=8, lds_rank=bool(rank))
         assert res.stats[i]["lds_budget"] == len(its) - 1
         assert res.stats[i]["nodes"] == sum(r.nodes for r in its)
     ctx.close()
 
 
-def test_first_mode_stops_at_the_least_budget():
+@pytest.mark.parametrize("rank", [0, 1], ids=["flat", "rank"])
+def test_first_mode_stops_at_the_least_budget(rank):
     insts = [x for x in I.batch_m4_7(24) if x.m <= 6][:10]
-    res, sols, ctx = M().solve(insts, mode=M().MSP_FIRST, order=M().MSP_LDS, lanes=8, max_seconds=120.0)
+    res, sols, ctx = M().solve(insts, mode=M().MSP_FIRST, order=M().MSP_LDS, lanes=8, max_seconds=120.0,
+                               lds_rank=rank)
     for i, inst in enumerate(insts):
         _, kern, g = O.reduce(inst.A, inst.d)
-        its = O.enumerate_lds(kern, g, inst.A, inst.d, lanes=8, first=True)
+        its = O.enumerate_lds(kern, g, inst.A, inst.d, lanes=8, first=True, lds_rank=bool(rank))
         assert res.stats[i]["lds_budget"] == len(its) - 1, i
         assert res.stats[i]["first_ms"] >= 0
         assert len(sols[i]) >= 1
         for x in sols[i].astype(np.int64):
             assert np.array_equal(inst.A.astype(np.int64) @ x, inst.d)
+    ctx.close()
+
+
+def test_lds_budget_cap_reports_ecap():
+    """An iterated search that reaches opts.lds_max before the tree is
+    exhausted says so (MSP_ECAP) instead of returning a partial set as
+    complete."""
+    inst = [x for x in I.batch_m4_7(24) if x.m == 5][0]
+    _, kern, g = O.reduce(inst.A, inst.d)
+    its = O.enumerate_lds(kern, g, inst.A, inst.d, lanes=8)
+    assert len(its) >= 3   # the tree needs budget 2 or more
+    res, sols, ctx = M().solve([inst], order=M().MSP_LDS, lanes=8, lds_max=1, max_seconds=120.0,
+                               allow=(M().MSP_OK, M().MSP_ECAP))
+    assert res.stats[0]["status"] == M().MSP_ECAP
+    assert res.stats[0]["nodes"] == its[0].nodes + its[1].nodes
     ctx.close()
 
 
