@@ -34,7 +34,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "enum nodes/s; time to all sols (m=9) & first sol (m=12), learned vs plain order"
-DRAM_BYTES_PER_NODE = (99.358720e6 + 323.379712e6) / 268321291   # enum_kernel<8, 8, 0>, ncu
+DRAM_BYTES_PER_NODE = (101.279488e6 + 322.009600e6) / 268321291   # enum_kernel<8, 8, 0>, ncu
 UNIT = "nodes/s"
 WORKLOAD = "batch of 64 fMSP instances, m~U{4..7}, n=10(m-1), D in {50,100,200}, all solutions"
 
