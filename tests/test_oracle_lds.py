@@ -159,3 +159,23 @@ def test_split_iteration_is_a_partition(inst, k, depth, rank):
         sols.append(sub.solutions)
     assert total == whole.nodes
     assert np.array_equal(O.sort_solutions(np.concatenate(sols)), whole.solutions)
+
+
+@pytest.mark.parametrize("inst", CASES[:8] + [I.batch_m4_7(64)[18]], ids=lambda x: x.tag)
+def test_rank_paths_are_a_subset_of_flat_paths(inst):
+    """A value other than the first costs at least one under the rank
+    reading, so with the same budget every path the rank iteration walks the
+    flat one walks too: fewer nodes, and the solutions reported up to budget
+    k are a subset of the flat ones (equal once both trees are exhausted)."""
+    _, kern, g = O.reduce(inst.A, inst.d)
+    got_r, got_f = set(), set()
+    for k in range(5):
+        r = O.enumerate(kern, g, inst.A, inst.d, lds=k, lds_rank=True)
+        f = O.enumerate(kern, g, inst.A, inst.d, lds=k, lds_rank=False)
+        assert r.nodes <= f.nodes and r.passed <= f.passed, k
+        got_r |= {x.tobytes() for x in r.solutions}
+        got_f |= {x.tobytes() for x in f.solutions}
+        assert got_r <= got_f, k
+    all_r = {x.tobytes() for it in O.enumerate_lds(kern, g, inst.A, inst.d, lds_rank=True) for x in it.solutions}
+    all_f = {x.tobytes() for it in O.enumerate_lds(kern, g, inst.A, inst.d, lds_rank=False) for x in it.solutions}
+    assert all_r == all_f
