@@ -8,10 +8,15 @@ Network: x (32 features) -> relu(x W1 + b1) (64) -> relu(h1 W2 + b2) (64)
 -> y = h2 W3 + b3 (8 outputs, 2 used: y0 = logit of P(the subtree holds a
 solution), y1 = predicted log(1 + nodes of the subtree)).
 
-Precision contract (the kernels' tensor-core path): inputs, weights and the
-hidden activations fed to the next layer are rounded to bfloat16 (round to
-nearest even); sums, biases, activations before rounding and all gradients
-are exact here (float64) where the kernels use float32.
+Precision contract (the kernels' tensor-core path): every product takes
+bfloat16 operands and accumulates in float32.  Forward: inputs, weights and
+the hidden activations fed to the next layer are rounded to bfloat16 (round
+to nearest even).  Backward (``round_grad_bf16=True``): the back-propagated
+signals dL/dy, dL/da2 and dL/da1 are rounded to bfloat16 where they enter a
+product (the next backward product and the weight-gradient products), while
+the bias gradients sum the unrounded signals.  Sums, biases, activations
+before rounding and all gradients are exact here (float64) where the kernels
+use float32.
 
 Loss per row: pos_weight * BCE(y0, found) for found rows, BCE for the
 others, plus 0.1 * (y1 - log1p(nodes))^2; the batch loss is the mean.
@@ -81,11 +86,18 @@ def forward(theta: np.ndarray, x: np.ndarray, round_bf16: bool = True):
 
 
 def loss_and_grad(theta: np.ndarray, x: np.ndarray, found: np.ndarray, lognodes: np.ndarray,
-                  pos_weight: float = 1.0, round_bf16: bool = True):
+                  pos_weight: float = 1.0, round_bf16: bool = True, round_grad_bf16: bool = False,
+                  scales: bool = False):
     """Mean loss over the rows and its gradient with respect to theta (the
     derivative is taken through the rounded values as constants, as the
-    kernels do)."""
+    kernels do).  round_grad_bf16: also round the back-propagated signals to
+    bfloat16 where they enter a product (the backward half of the precision
+    contract).  scales: also return, per parameter, the sum over the rows of
+    the absolute values of the terms that make up its gradient (|A|^T |G|
+    for a weight, sum |G| for a bias) -- the size against which rounding
+    errors of that element are measured."""
     r = bf16 if round_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+    rg = bf16 if round_grad_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
     p = unpack(theta)
     y, c = forward(theta, x, round_bf16)
     B = x.shape[0]
@@ -98,16 +110,32 @@ def loss_and_grad(theta: np.ndarray, x: np.ndarray, found: np.ndarray, lognodes:
     dy = np.zeros_like(y)
     dy[:, 0] = w * (1.0 / (1.0 + np.exp(-z)) - f) / B
     dy[:, 1] = 2.0 * NODE_WEIGHT * diff / B
-    g = {}
-    g["W3"] = c["h2b"].T @ dy
+    g, sc = {}, {}
+    dyr = rg(dy)
+    g["W3"] = c["h2b"].T @ dyr
     g["b3"] = dy.sum(axis=0)
-    dh2 = (dy @ r(p["W3"]).T) * (c["a2"] > 0)
-    g["W2"] = c["h1b"].T @ dh2
+    dh2 = (dyr @ r(p["W3"]).T) * (c["a2"] > 0)
+    dh2r = rg(dh2)
+    g["W2"] = c["h1b"].T @ dh2r
     g["b2"] = dh2.sum(axis=0)
-    dh1 = (dh2 @ r(p["W2"]).T) * (c["a1"] > 0)
-    g["W1"] = c["xb"].T @ dh1
+    dh1 = (dh2r @ r(p["W2"]).T) * (c["a1"] > 0)
+    dh1r = rg(dh1)
+    g["W1"] = c["xb"].T @ dh1r
     g["b1"] = dh1.sum(axis=0)
-    return loss, pack(g)
+    if not scales:
+        return loss, pack(g)
+    sc["W3"] = np.abs(c["h2b"]).T @ np.abs(dyr)
+    sc["b3"] = np.abs(dy).sum(axis=0)
+    sc["W2"] = np.abs(c["h1b"]).T @ np.abs(dh2r)
+    sc["b2"] = np.abs(dh2).sum(axis=0)
+    sc["W1"] = np.abs(c["xb"]).T @ np.abs(dh1r)
+    sc["b1"] = np.abs(dh1).sum(axis=0)
+    return loss, pack(g), pack(sc)
+
+
+def blocks(theta: np.ndarray) -> dict:
+    """The parameter vector split into its named blocks (flat float64 views)."""
+    return {name: v.reshape(-1) for name, v in unpack(theta).items()}
 
 
 def score(y: np.ndarray) -> np.ndarray:
