@@ -339,7 +339,8 @@ MSP_API msp_status msp_fp64_peak(msp_ctx *ctx, double *dfma_per_s);
  * msp_reduce(), so the result equals msp_export_reduced() of that path.
  *   m, n      1 <= m <= 32, m <= n <= 127; larger sizes return MSP_EINVAL
  *   A, d      device pointers: A int32 m x n row-major, d int64[m] (inputs)
- *   N, delta, eta, max_iter   as in msp_opts
+ *   N, delta, eta, max_iter   as in msp_opts; the LLL loop's device-time
+ *             cap is msp_opts' default max_seconds, 600 s (MSP_ECAP after)
  *   basis     device pointer, int64 (n+1) x (m+n+1) (output, one reduced
  *             vector per row)
  *   stream    cudaStream_t (NULL: default stream); the call synchronises it

@@ -659,8 +659,8 @@ int oracle_enumerate_bounds(int dd, int dim, const double *mu, const double *B, 
 }
 
 /* ------------------------------------------------------------------------ */
-/* 6. BKZ-beta on the kernel basis (Sec. 2 names "LLL or blockwise           */
-/* Korkine-Zolotarev reduction" for step 1; the paper gives no parameters).  */
+/* 6. BKZ-beta on the kernel basis (Sec. 2 allows block reduction in place  */
+/* of LLL for step 1 and gives no parameters).                               */
 /* Readings (R14):                                                           */
 /*   - BKZ runs on the kept kernel basis after LLL and extraction (the same */
 /*     lattice the enumeration walks; the rows scaled by N play no part).   */

@@ -517,8 +517,8 @@ __global__ void __launch_bounds__(32) extract_gso_kernel(Pools P, int gso_only) 
 }
 
 // ---------------------------------------------------------------------------
-// BKZ-beta of the kernel basis (Sec. 2: "LLL or blockwise Korkine-Zolotarev
-// reduction"), one warp per instance, after extraction.  A tour visits the
+// BKZ-beta of the kernel basis (Sec. 2 offers block reduction as the
+// alternative to LLL for step 1), one warp per instance, after extraction.  A tour visits the
 // blocks [k, h), h = min(k + beta, dd), k = 0 .. dd-2: the Gram-Schmidt data
 // of the whole basis is rebuilt (exact Gram matrix, Eq. (4) divided form),
 // the block's shortest nonzero projected vector is searched by

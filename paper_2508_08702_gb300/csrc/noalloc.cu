@@ -97,7 +97,8 @@ extern "C" MSP_API msp_status msp_reduce_lattice_noalloc(int m, int n, const int
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        lll_kernel<<<1, 32, 0, st>>>(P, delta, eta, max_iter, 60ULL * 1000000000ULL);
+        // the same device-time cap as msp_reduce with default options (600 s)
+        lll_kernel<<<1, 32, 0, st>>>(P, delta, eta, max_iter, 600ULL * 1000000000ULL);
         e = cudaGetLastError();
     }
     InstDesc out;

@@ -1,5 +1,5 @@
-"""Pins for the oracle's BKZ reduction of the kernel basis (Sec. 2: "LLL or
-blockwise Korkine-Zolotarev reduction").
+"""Pins for the oracle's BKZ reduction of the kernel basis (Sec. 2 allows
+block reduction in place of LLL for step 1).
 
 Checked against things the C code does not compute itself:
   * the reduced basis spans the same lattice: an integer matrix U with
