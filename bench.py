@@ -34,6 +34,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "enum nodes/s; time to all sols (m=9) & first sol (m=12), learned vs plain order"
+# the autotuner's grid for the batch (coordinate descent, library defaults first)
+TUNE_GRID = {"lanes": (8, 16), "warps_per_block": (8, 4), "blocks_per_sm": (0, 1),
+             "split_target": (0, 256, 4096, 16384)}
 DRAM_BYTES_PER_NODE = (101.279488e6 + 322.009600e6) / 268321291   # enum_kernel<8, 8, 0>, ncu
 UNIT = "nodes/s"
 WORKLOAD = "batch of 64 fMSP instances, m~U{4..7}, n=10(m-1), D in {50,100,200}, all solutions"
@@ -55,22 +58,124 @@ def parse():
                         "first-solution configurations once (one GPU)")
     p.add_argument("--bkz", type=int, default=None, help="BKZ block size (default: 0 for batch64, 10 otherwise)")
     p.add_argument("--cap", type=float, default=None, help="time cap in seconds for the other workloads")
-    p.add_argument("--orders", default="plain,learned,lds", help="first-solution workloads: orders to time")
+    p.add_argument("--orders", default="plain,learned,lds,lds_learned",
+                   help="first-solution workloads: orders to time")
+    p.add_argument("--no-tune", action="store_true", help="batch64: library defaults instead of the autotuner")
+    p.add_argument("--no-headline", action="store_true",
+                   help="batch64: skip the m=9 all-solutions and m=12 first-solution runs")
     return p.parse_args()
 
 
 # The paper's larger configurations (synthetic stand-ins, seeds in instances.py):
-# name -> (generator, mode, default time cap in seconds)
+# name -> (generator spec, mode, default time cap in seconds); a spec is the
+# name of a generator of instances.py, or (name, positional arguments)
 WORKLOADS = {
     "m8_all": ("m8_n70", "all", 300.0),     # m=8, n=70, D=200, 16 instances
     "m9_all": ("m9_n80", "all", 1200.0),    # m=9, n=80, D=100, 8 instances, 40 ones planted
     "m8_first": ("m8_n70", "first", 120.0),
     "m12_first": ("m12_n110", "first", 60.0),   # m=12, n=110, D=100, 4 instances
-    "m10d50_first": ("m10_n90_d50", "first", 30.0),    # m=10, n=90, D=50, 4 instances
-    "m11d50_first": ("m11_n100_d50", "first", 30.0),   # m=11, n=100, D=50, 4 instances
-    "m12d50_first": ("m12_n110_d50", "first", 60.0),   # m=12, n=110, D=50 (the paper's m=12 row), 4 instances
-    "cd8_all": ("cd8", "all", 600.0),       # Cornuejols-Dawande m=8 (nothing planted), 16 instances
+    "m10d50_first": ("m10_n90_d50", "first", 30.0),    # m=10, n=90, D=50, 4 planted instances
+    "m11d50_first": ("m11_n100_d50", "first", 30.0),   # m=11, n=100, D=50, 4 planted instances
+    "m12d50_first": ("m12_n110_d50", "first", 60.0),   # m=12, n=110, D=50, 4 planted instances
+    "cd8_all": (("cd_batch", (8, 16)), "all", 600.0),   # Cornuejols-Dawande m=8 (nothing planted), 16 instances
+    # centred right-hand sides (the paper's instance library's solution counts), D = 50
+    "m7c50_all": (("centred", (7, 50)), "all", 120.0),
+    "m8c50_all": (("centred", (8, 50)), "all", 300.0),
+    "m9c100_all": (("centred", (9, 100)), "all", 1200.0),
+    "m10c50_first": (("centred", (10, 50)), "first", 30.0),
+    "m11c50_first": (("centred", (11, 50)), "first", 60.0),
+    "m12c50_first": (("centred", (12, 50)), "first", 120.0),
 }
+
+
+def make_instances(spec):
+    """The instances of a WORKLOADS generator spec."""
+    from paper_2508_08702_gb300 import instances as I
+    if isinstance(spec, str):
+        return getattr(I, spec)()
+    name, args = spec
+    return getattr(I, name)(*args)
+
+
+def _verified(ctx, i, inst):
+    """Every reported x solves A x = d exactly; is the planted x among them?"""
+    import numpy as np
+    xs = ctx.msp_solutions(i).astype(np.int64)
+    ok = all(np.array_equal(x @ inst.A.T.astype(np.int64), inst.d) for x in xs)
+    planted = inst.planted is not None and any(np.array_equal(inst.planted, x) for x in xs)
+    return ok, planted, len(xs)
+
+
+def run_all_solutions(insts, cap, **opts):
+    """Wall time from the reduction to the verified solutions of the whole
+    batch (the paper's timings include the reduction), one launch."""
+    import torch
+    from paper_2508_08702_gb300 import instances as I
+    from paper_2508_08702_gb300 import msp as M
+    pk = I.pack(insts)
+    ctx = M.Context(max_seconds=cap + 60, **opts)
+    ctx.msp_build_lattice(pk.dims, pk.A, pk.d)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.msp_reduce()
+    res = ctx.msp_enumerate(M.MSP_ALL, M.MSP_PLAIN, cap, allow=(M.MSP_OK, M.MSP_ETIMEOUT))
+    wall = time.perf_counter() - t0
+    ph = ctx.msp_phase_ms()
+    checks = [_verified(ctx, i, x) for i, x in enumerate(insts)]
+    out = {"wall_s": round(wall, 3), "complete": res.status == M.MSP_OK, "status": res.status,
+           "lanes": ctx.lanes, "phase_ms": {k: round(v, 1) for k, v in ph.items()},
+           "nodes": res.total["nodes"], "nodes_per_s": res.total["nodes"] / max(ph["enumerate"] / 1e3, 1e-9),
+           "solutions": [c[2] for c in checks], "all_verified": all(c[0] for c in checks),
+           "planted_found": sum(c[1] for c in checks),
+           "proved_infeasible": sum(1 for c in checks if c[2] == 0) if res.status == M.MSP_OK else 0}
+    ctx.close()
+    return out
+
+
+def train_scorer():
+    """The subtree scorer, trained on the device on 256 generated m = 5..7
+    instances (seeds disjoint from every evaluation set)."""
+    from paper_2508_08702_gb300 import instances as I
+    from paper_2508_08702_gb300 import learn
+    t0 = time.perf_counter()
+    data = learn.collect(I.training_set(256))
+    theta, _ = learn.train(data, steps=4000)
+    return theta, round(time.perf_counter() - t0, 2)
+
+
+def run_first_solution(insts, cap, orders, theta=None, **opts):
+    """Per order: wall time of reduction + search, and each instance's time
+    to its first verified solution from the start of the enumeration."""
+    import numpy as np
+    import torch
+    from paper_2508_08702_gb300 import instances as I
+    from paper_2508_08702_gb300 import msp as M
+    pk = I.pack(insts)
+    names = {"plain": M.MSP_PLAIN, "learned": M.MSP_LEARNED, "lds": M.MSP_LDS, "lds_learned": M.MSP_LDS_LEARNED}
+    runs = {}
+    for name in orders:
+        ctx = M.Context(max_seconds=cap + 60, **opts)
+        if name in ("learned", "lds_learned"):
+            ctx.msp_set_scorer(theta)
+        ctx.msp_build_lattice(pk.dims, pk.A, pk.d)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.msp_reduce()
+        res = ctx.msp_enumerate(M.MSP_FIRST, names[name], cap, allow=(M.MSP_OK, M.MSP_ETIMEOUT, M.MSP_ECAP))
+        wall = time.perf_counter() - t0
+        ph = ctx.msp_phase_ms()
+        fm = [s["first_ms"] for s in res.stats]
+        solved = [f for f in fm if f >= 0]
+        checks = [_verified(ctx, i, x) for i, x in enumerate(insts)]
+        runs[name] = {"wall_s": round(wall, 3), "reduce_ms": round(ph["reduce"], 1),
+                      "solved": len(solved), "of": len(fm),
+                      "first_s": [round(f / 1e3, 3) if f >= 0 else None for f in fm],
+                      "median_first_s": round(float(np.median(fm)) / 1e3, 3) if len(solved) == len(fm) else None,
+                      "nodes": res.total["nodes"], "all_verified": all(c[0] for c in checks)}
+        if name.startswith("lds"):
+            runs[name]["lds_budget"] = [s["lds_budget"] for s in res.stats]
+        ctx.close()
+    return runs
 
 
 def extended(args):
@@ -78,88 +183,41 @@ def extended(args):
     to the verified solutions (the paper's timings include the reduction),
     per instance and for the batch; first-solution workloads compare the
     queue orders."""
-    import numpy as np
     import torch
     from paper_2508_08702_gb300 import build as B
     from paper_2508_08702_gb300 import instances as I
-    from paper_2508_08702_gb300 import learn
-    from paper_2508_08702_gb300 import msp as M
 
     B.build()
     gen, mode, cap = WORKLOADS[args.workload]
     cap = args.cap or cap
     bkz = 10 if args.bkz is None else args.bkz
-    insts = I.cd_batch(8, 16) if gen == "cd8" else getattr(I, gen)()
-    pk = I.pack(insts)
-    opts = dict(bkz_beta=bkz, max_seconds=cap + 60)
+    insts = make_instances(gen)
+    opts = dict(bkz_beta=bkz)
     if args.lanes:
         opts["lanes"] = args.lanes
-    data = ("synthetic Cornuejols-Dawande instances (d = floor(sum a / 2), nothing planted)" if gen == "cd8"
+    data = ("synthetic, centred right-hand side d = floor(sum a / 2), nothing planted" if insts[0].planted is None
             else "synthetic (planted instances of the paper's shapes)")
     out = {"workload": args.workload, "instances": len(insts), "m": insts[0].m, "n": insts[0].n, "D": insts[0].D,
            "bkz_beta": bkz, "cap_s": cap, "data": data,
            "gpu": torch.cuda.get_device_name()}
     clocks = Clocks(torch.cuda.current_device())
-
-    def verified(ctx, i, inst):
-        xs = ctx.msp_solutions(i).astype(np.int64)
-        ok = all(np.array_equal(x @ inst.A.T.astype(np.int64), inst.d) for x in xs)
-        planted = inst.planted is not None and any(np.array_equal(inst.planted, x) for x in xs)
-        return ok, planted, len(xs)
-
     if mode == "all":
-        ctx = M.Context(**opts)
-        ctx.msp_build_lattice(pk.dims, pk.A, pk.d)
-        torch.cuda.synchronize()
         clocks.start()
-        t0 = time.perf_counter()
-        ctx.msp_reduce()
-        res = ctx.msp_enumerate(M.MSP_ALL, M.MSP_PLAIN, cap, allow=(M.MSP_OK, M.MSP_ETIMEOUT))
-        wall = time.perf_counter() - t0
+        r = run_all_solutions(insts, cap, **opts)
         out["clocks"] = clocks.stop()
-        ph = ctx.msp_phase_ms()
-        checks = [verified(ctx, i, x) for i, x in enumerate(insts)]
-        out.update({"metric": "time to all solutions (reduction + enumeration), whole batch", "value": wall,
-                    "unit": "s", "higher_is_better": False, "complete": res.status == M.MSP_OK,
-                    "status": res.status, "lanes": ctx.lanes, "phase_ms": {k: round(v, 1) for k, v in ph.items()},
-                    "nodes": res.total["nodes"], "nodes_per_s": res.total["nodes"] / (ph["enumerate"] / 1e3),
-                    "solutions": [c[2] for c in checks], "all_verified": all(c[0] for c in checks),
-                    "planted_found": sum(c[1] for c in checks),
-                    "proved_infeasible": sum(1 for c in checks if c[2] == 0) if res.status == M.MSP_OK else 0})
-        ctx.close()
+        out.update({"metric": "time to all solutions (reduction + enumeration), whole batch",
+                    "value": r["wall_s"], "unit": "s", "higher_is_better": False}, **r)
     else:
         theta = None
-        if "learned" in args.orders:
-            t0 = time.perf_counter()
-            data = learn.collect(I.training_set(256))
-            theta, _ = learn.train(data, steps=4000)
-            out["scorer_training_s"] = round(time.perf_counter() - t0, 2)
-        names = {"plain": M.MSP_PLAIN, "learned": M.MSP_LEARNED, "lds": M.MSP_LDS}
-        runs = {}
+        orders = args.orders.split(",")
+        if any("learned" in o for o in orders):
+            theta, out["scorer_training_s"] = train_scorer()
         clocks.start()
-        for name in args.orders.split(","):
-            ctx = M.Context(**opts)
-            if name == "learned":
-                ctx.msp_set_scorer(theta)
-            ctx.msp_build_lattice(pk.dims, pk.A, pk.d)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ctx.msp_reduce()
-            res = ctx.msp_enumerate(M.MSP_FIRST, names[name], cap, allow=(M.MSP_OK, M.MSP_ETIMEOUT))
-            wall = time.perf_counter() - t0
-            ph = ctx.msp_phase_ms()
-            fm = [s["first_ms"] for s in res.stats]
-            solved = [f for f in fm if f >= 0]
-            checks = [verified(ctx, i, x) for i, x in enumerate(insts)]
-            runs[name] = {"wall_s": round(wall, 3), "reduce_ms": round(ph["reduce"], 1),
-                          "solved": len(solved), "first_ms": [round(f, 1) for f in fm],
-                          "median_first_ms": float(np.median(fm)) if len(solved) == len(fm) else None,
-                          "nodes": res.total["nodes"], "all_verified": all(c[0] for c in checks)}
-            ctx.close()
+        runs = run_first_solution(insts, cap, orders, theta, **opts)
         out["clocks"] = clocks.stop()
-        med = [r["median_first_ms"] for r in runs.values() if r["median_first_ms"] is not None]
+        med = [r["median_first_s"] for r in runs.values() if r["median_first_s"] is not None]
         out.update({"metric": "median time to an instance's first solution (from the enumeration start), "
-                              "best queue order", "value": min(med) / 1e3 if med else None, "unit": "s",
+                              "best queue order", "value": min(med) if med else None, "unit": "s",
                     "higher_is_better": False, "orders": runs})
     print(json.dumps(out), flush=True)
 
@@ -256,34 +314,126 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------
-def oracle_nodes_per_s(instances, seconds: float):
+def oracle_nodes_per_s(instances, seconds: float, lanes: int = 32, min_seconds: float = 0.0):
     """The CPU oracle as it stands, one thread, on instances taken in order
-    until `seconds` of work; returns (nodes/s, nodes, seconds, count)."""
+    until `seconds` of work (whole passes over the list are repeated until
+    `min_seconds` have passed); returns (nodes/s, nodes, seconds, count)."""
     from oracle import oracle as O
     nodes = 0
     t0 = time.perf_counter()
     done = 0
-    for inst in instances:
-        r = O.solve(inst.A, inst.d).result
-        nodes += r.nodes
-        done += 1
-        if time.perf_counter() - t0 > seconds:
+    while True:
+        for inst in instances:
+            r = O.solve(inst.A, inst.d, lanes=lanes).result
+            nodes += r.nodes
+            done += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        dt = time.perf_counter() - t0
+        if dt > seconds or dt >= min_seconds or not instances:
             break
-    dt = time.perf_counter() - t0
     return nodes / dt, nodes, dt, done
 
 
 def cpu_sample(instances):
     """Bounded sample of the batch for the oracle: the instances with m <= 6
-    (the m = 7 instances take the oracle 2 to 70 s each)."""
+    (about 2.5 s of one core in all; the m = 7 instances take the oracle 2
+    to 70 s each).  The GPU's nodes/s is reported on the same sample."""
     return [x for x in instances if x.m <= 6]
 
 
 def cpu_baseline_sample(instances):
-    """The oracle baseline's sample (10 to 30 s of one core): the instances
-    with m <= 6 and the m = 7 ones with D >= 100 (2 to 7 s each; with D = 50
-    they take 30 to 70 s)."""
+    """The instances with m <= 6 and the m = 7 ones with D >= 100 (2 to 7 s
+    each; with D = 50 they take 30 to 70 s)."""
     return [x for x in instances if x.m <= 6 or (x.m == 7 and getattr(x, "D", 0) >= 100)]
+
+
+def cpu_baseline(sample, seconds: float, lanes: int):
+    """The oracle, one thread, repeated passes over the sample (10 to
+    `seconds` s of CPU work), and the same instances one per core."""
+    v, nodes, dt, cnt = oracle_nodes_per_s(sample, seconds, lanes=lanes, min_seconds=10.0)
+    host = host_cpu()
+    out = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"the {len(sample)} batch instances with m<=6, {cnt} runs in order ({nodes} nodes, "
+                     f"{dt:.1f} s), LLL + enumeration, one thread, |w|_1 order of {lanes}-lane walkers",
+           "host": host}
+    if host["nproc"] and host["nproc"] > 1:
+        pv, pn, pdt = oracle_parallel_nodes_per_s(sample, host["nproc"])
+        out["parallel"] = {"value": pv, "unit": UNIT, "cores": host["nproc"],
+                           "sample": f"the same {len(sample)} instances, one instance per core "
+                                     f"({pn} nodes, {pdt:.1f} s wall)"}
+    return out
+
+
+def gpu_nodes_per_s(instances, opts, steps, flush):
+    """Device-timed nodes/s of whole steps on a batch (after one warm-up
+    step, L2 flushed before each step); returns (nodes/s, nodes per step)."""
+    import torch
+    from paper_2508_08702_gb300 import instances as I
+    from paper_2508_08702_gb300 import msp as M
+    pk = I.pack(instances)
+    ctx = M.Context(**opts)
+    A_dev = torch.from_numpy(pk.A).cuda()
+    d_dev = torch.from_numpy(pk.d).cuda()
+    stream = torch.cuda.current_stream()
+    ms, nodes = 0.0, 0
+    for k in range(max(1, min(steps, 5)) + 1):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.msp_build_lattice(pk.dims, A_dev, d_dev)
+        ctx.msp_run_async()
+        e1.record(stream)
+        res = ctx.msp_wait()
+        if k > 0:
+            ms += e0.elapsed_time(e1)
+            nodes += res.total["nodes"]
+    per_step = res.total["nodes"]
+    ctx.close()
+    return nodes / (ms / 1e3), per_step
+
+
+def launch_desc(opts, lanes):
+    """The enumeration launch in effect: the options given and the lanes chosen."""
+    d = {k: v for k, v in opts.items()}
+    d["lanes"] = lanes
+    return d
+
+
+# the headline's paper configurations (synthetic stand-ins, seeds in instances.py)
+HEADLINE_FIRST = (
+    ("m12_n110_d100", "m12_n110", 30.0, "m=12, n=110, D=100, 4 planted instances (seeds 5000..5003)"),
+    ("m12_n110_d50_centred", ("centred", (12, 50)), 60.0,
+     "m=12, n=110, D=50, 4 instances with the centred right-hand side (seeds 61250..61253): the paper's m=12 row"),
+)
+
+
+def headline(args, clocks_index=0):
+    """The metric's two headline times, measured in the same run as the node
+    rate: all solutions of the m = 9, n = 80, D = 100 batch (8 instances,
+    BKZ-10; one warm-up on one m = 8 instance, which runs the same kernels),
+    and the time to the first solution at m = 12 under the plain, learned and
+    limited-discrepancy orders (BKZ-10, a cap per run)."""
+    from paper_2508_08702_gb300 import instances as I
+    out = {}
+    clocks = Clocks(clocks_index)
+    run_all_solutions(I.m8_n70(1), 120.0, bkz_beta=10)   # warm-up
+    clocks.start()
+    r = run_all_solutions(I.m9_n80(8), 1200.0, bkz_beta=10)
+    r["clocks"] = clocks.stop()
+    r["workload"] = "m=9, n=80, D=100, 8 instances, planted x with 40 ones (seeds 4000..4007), BKZ-10, all solutions"
+    out["m9_all"] = r
+    orders = args.orders.split(",")
+    theta, train_s = train_scorer() if any("learned" in o for o in orders) else (None, 0.0)
+    first = {"scorer_training_s": train_s, "bkz_beta": 10, "workloads": {}}
+    clocks.start()
+    for key, gen, cap, desc in HEADLINE_FIRST:
+        runs = run_first_solution(make_instances(gen), cap, orders, theta, bkz_beta=10)
+        first["workloads"][key] = {"workload": desc, "cap_s": cap, "orders": runs}
+    first["clocks"] = clocks.stop()
+    out["first_solution"] = first
+    return out
 
 
 def _oracle_solve_nodes(Ad):
@@ -325,17 +475,19 @@ def reference_arm(args, rank, world):
     from paper_2508_08702_gb300 import instances as I
     if rank != 0:
         return
+    # the same sample as the main arm's cpu_baseline and its gpu_same_sample
     insts = cpu_sample(I.batch_m4_7(64))
     for _ in range(args.warmup):
-        oracle_nodes_per_s(insts[:4], 1e9)
+        oracle_nodes_per_s(insts[:4], 1e9, lanes=8)
     vals, nodes_tot, t_tot = [], 0, 0.0
     for _ in range(args.steps):
-        v, nodes, dt, _ = oracle_nodes_per_s(insts, 1e9)
+        v, nodes, dt, _ = oracle_nodes_per_s(insts, 1e9, lanes=8)
         vals.append(v)
         nodes_tot += nodes
         t_tot += dt
     value = nodes_tot / t_tot
-    sample = f"{len(insts)} of the 64 batch instances (those with m<=6), LLL + enumeration, one thread"
+    sample = (f"{len(insts)} of the 64 batch instances (those with m<=6), LLL + enumeration, one thread, "
+              f"|w|_1 order of 8-lane walkers")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
@@ -384,6 +536,19 @@ def main():
     insts = I.batch_m4_7(64, first_seed=2000 + 64 * rank)[:args.instances]
     pk = I.pack(insts)
     kw = {} if args.lanes is None else {"lanes": args.lanes}
+    tuning = None
+    if not args.no_tune:
+        # the launch shape and split of this batch, picked by the autotuner
+        # (coordinate descent over lanes, warps per block, blocks per SM and
+        # the split target; device time of whole steps)
+        from paper_2508_08702_gb300 import tune
+        grid = dict(TUNE_GRID)
+        if args.lanes is not None:
+            grid["lanes"] = (args.lanes,)
+        t0 = time.perf_counter()
+        tuning = tune.tune(insts, grid=grid, strategy="descent", repeats=1)
+        tuning["seconds"] = round(time.perf_counter() - t0, 1)
+        kw.update(tuning["opts"])
     ctx = M.Context(**kw)
     A_dev = torch.from_numpy(pk.A).to(dev)
     d_dev = torch.from_numpy(pk.d).to(dev)
@@ -477,29 +642,32 @@ def main():
                    "l2": "flushed between steps (512 MB write)",
                    "nodes_per_step": res.total["nodes"], "solutions_per_step": res.total["solutions"],
                    "phase_ms": {k: round(v, 3) for k, v in ph.items()},
+                   "split_levels_median": float(np.median([s["kernel_rank"] - s["split_level"] for s in res.stats])),
+                   "launch": launch_desc(kw, ctx.lanes),
                    "wall_s_timed_region": round(wall, 3)},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if tuning is not None:
+        line["config"]["autotuned"] = {
+            "strategy": tuning["strategy"], "seconds": tuning["seconds"], "chosen": tuning["opts"],
+            "table": [dict(r["opts"], ms=round(r["ms"], 2) if math.isfinite(r["ms"]) else None)
+                      for r in tuning["table"]]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = cpu_baseline_sample(insts)
-        v, nodes, dt, cnt = oracle_nodes_per_s(sample, args.cpu_seconds)
-        host = host_cpu()
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {cnt} of the {len(sample)} batch instances with m<=6 or "
-                                          f"(m=7, D>=100) ({nodes} nodes, {dt:.1f} s), LLL + enumeration, "
-                                          f"one thread",
-                                "host": host}
-        if host["nproc"] and host["nproc"] > 1:
-            pv, pn, pdt = oracle_parallel_nodes_per_s(sample[:cnt], host["nproc"])
-            line["cpu_baseline"]["parallel"] = {
-                "value": pv, "unit": UNIT, "cores": host["nproc"],
-                "sample": f"the same {cnt} instances, one instance per core ({pn} nodes, {pdt:.1f} s wall)"}
+        # the GPU on exactly the oracle's sample, so that the two divide like for like
+        sample = cpu_sample(insts)
+        gv, gnodes = gpu_nodes_per_s(sample, kw, args.steps, flush)
+        line["cpu_baseline"] = cpu_baseline(sample, args.cpu_seconds, ctx.lanes)
+        line["cpu_baseline"]["gpu_same_sample"] = {
+            "value": gv, "unit": UNIT, "nodes_per_step": gnodes,
+            "sample": f"the same {len(sample)} instances on the GPU, device time of whole steps"}
+    ctx.close()
+    if rank == 0 and world == 1 and not args.no_headline:
+        line.update(headline(args, clocks_index=local))
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

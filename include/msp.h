@@ -64,8 +64,11 @@ typedef enum { MSP_ALL = 0, MSP_FIRST = 1 } msp_mode;      /* all solutions / st
  * centre) only while the path above carries fewer than k such
  * discrepancies, and report the leaves with exactly k; MSP_FIRST stops an
  * instance at its first solution, MSP_ALL when an iteration held no value
- * back (every solution is then reported exactly once). */
-typedef enum { MSP_PLAIN = 0, MSP_LEARNED = 1, MSP_LDS = 2 } msp_order;
+ * back (every solution is then reported exactly once).  LDS_LEARNED: limited
+ * discrepancy search whose iterations take their subtrees in the scorer's
+ * order (as LEARNED does; the same nodes and solutions as LDS, possibly
+ * sooner). */
+typedef enum { MSP_PLAIN = 0, MSP_LEARNED = 1, MSP_LDS = 2, MSP_LDS_LEARNED = 3 } msp_order;
 typedef enum { MSP_HOST = 0, MSP_DEVICE = 1 } msp_memory;  /* where A and d live           */
 
 /* Options.  msp_default_opts() fills the defaults given in brackets. */

@@ -207,8 +207,12 @@ void enum_launch_shape(const msp_ctx* c, int* blocks, int* threads) {
     int t = c->o.warps_per_block * 32;
     while (t > 32 && enum_smem_bytes(c->lanes, t, c->Kmax) > c->smem_optin) t -= 32;
     *threads = t;
+    // blocks per SM: the option, at most as many as can be resident (the
+    // walkers are persistent: a block that cannot start would only start
+    // once others have finished)
+    const int fit = std::max(1, enum_blocks_per_sm(c->lanes, t, c->dimMax, c->Kmax));
     int bps = c->o.blocks_per_sm;
-    if (bps <= 0) bps = std::max(1, enum_blocks_per_sm(c->lanes, t, c->dimMax, c->Kmax));
+    bps = bps <= 0 ? fit : std::min(bps, fit);
     *blocks = c->sms * bps;
 }
 
@@ -621,7 +625,7 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
     c->launches += 2;
     // subtree features and queue order: the first-solution mode interleaves the
     // instances by rank (depth-first rank, or the scorer's rank when learned)
-    const bool learned = (order == MSP_LEARNED) && c->scorer_set;
+    const bool learned = (order == MSP_LEARNED || order == MSP_LDS_LEARNED) && c->scorer_set;
     const bool want_features = c->o.log_features || learned;
     Pools Pq = c->P;
     c->features_valid = false;
@@ -673,7 +677,7 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
 // the per-instance counters: an instance is finished once it has a solution
 // (MSP_FIRST) or once an iteration held no value back for want of budget
 // (its tree is exhausted); finished instances get no subtrees afterwards.
-static msp_status run_lds(msp_ctx* c, int mode, double time_cap_s) {
+static msp_status run_lds(msp_ctx* c, int mode, int order, double time_cap_s) {
     const int n = c->count;
     msp_status s = ensure(c, c->skip, (size_t)n, "skip");
     if (s != MSP_OK) return s;
@@ -687,7 +691,7 @@ static msp_status run_lds(msp_ctx* c, int mode, double time_cap_s) {
     cudaError_t e = cudaMemsetAsync(c->skip.p, 0, (size_t)n, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "lds skip");
     for (int k = k0; k <= k1; ++k) {
-        if ((s = queue_enumerate(c, mode, MSP_LDS, time_cap_s, k, k != k0)) != MSP_OK) return s;
+        if ((s = queue_enumerate(c, mode, order, time_cap_s, k, k != k0)) != MSP_OK) return s;
         Ctrl ctl;
         e = cudaStreamSynchronize(c->st);
         if (e == cudaSuccess) e = cudaMemcpy(cn.data(), c->cnt.p, sizeof(InstCounters) * n, cudaMemcpyDeviceToHost);
@@ -955,8 +959,10 @@ msp_status msp_enumerate(msp_ctx* c, int mode, int order, double time_cap_s, msp
     if (!c) return MSP_EINVAL;
     if (c->state < 2) return fail(c, MSP_ESTATE, "msp_enumerate before msp_reduce");
     if (mode != MSP_ALL && mode != MSP_FIRST) return fail(c, MSP_EINVAL, "bad mode");
-    if (order != MSP_PLAIN && order != MSP_LEARNED && order != MSP_LDS) return fail(c, MSP_EINVAL, "bad order");
-    msp_status s = order == MSP_LDS ? run_lds(c, mode, time_cap_s) : queue_enumerate(c, mode, order, time_cap_s);
+    if (order != MSP_PLAIN && order != MSP_LEARNED && order != MSP_LDS && order != MSP_LDS_LEARNED)
+        return fail(c, MSP_EINVAL, "bad order");
+    const bool lds = order == MSP_LDS || order == MSP_LDS_LEARNED;
+    msp_status s = lds ? run_lds(c, mode, order, time_cap_s) : queue_enumerate(c, mode, order, time_cap_s);
     if (s != MSP_OK) return s;
     return msp_wait(c, stats, total);
 }

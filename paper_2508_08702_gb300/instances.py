@@ -146,16 +146,31 @@ def bounded(seed: int, m: int, n: int, D: int, bounds=(1, 2, 3)) -> Instance:
     return Instance(A=A, d=d, planted=x, seed=seed, D=D, tag=f"bounded_m{m}n{n}D{D}_{seed}", r=r)
 
 
-def cornuejols_dawande(seed: int, m: int) -> Instance:
+def cornuejols_dawande(seed: int, m: int, D: int = 100) -> Instance:
     """The original market split instances (Sec. 1): n = 10(m-1), a_ij
-    uniform in [0, 100), d_i = floor(sum_j a_ij / 2).  Nothing is planted, so
-    feasibility is not known in advance: at m = 3..6 about a third of them
-    have no solution, and answering those takes an exhaustive search."""
+    uniform in [0, D) (D = 100 in the original), d_i = floor(sum_j a_ij / 2).
+    Nothing is planted, so feasibility is not known in advance: at m = 3..6
+    about a third of them have no solution, and answering those takes an
+    exhaustive search."""
     rng = np.random.default_rng(seed)
     n = 10 * (m - 1)
-    A = rng.integers(0, 100, size=(m, n)).astype(np.int32)
+    A = rng.integers(0, D, size=(m, n)).astype(np.int32)
     d = (A.astype(np.int64).sum(axis=1) // 2).astype(np.int64)
-    return Instance(A=A, d=d, planted=None, seed=seed, D=100, tag=f"cd_m{m}_{seed}")
+    return Instance(A=A, d=d, planted=None, seed=seed, D=D, tag=f"cd_m{m}_D{D}_{seed}")
+
+
+def centred(m: int, D: int = 50, count: int = 4, first_seed: int = 60000) -> List[Instance]:
+    """Stand-ins for the paper's instance library at the rows of its timing
+    table (Sec. 4): a_ij uniform in [0, D), n = 10(m-1) and the centred
+    right-hand side d_i = floor(sum_j a_ij / 2) of the original construction;
+    seeds first_seed + 100 m + D + i.  Their solution counts match the
+    paper's table where it lists them (m = 7..9: e.g. 170-270 solutions per
+    instance at m = 7, D = 50 and 670-860 at m = 8, D = 50, against the
+    table's 25-306 and 752-1265), while instances with a planted Bernoulli(1/2)
+    x have a tenth as many (7-66 and 10-199): their d lies off the centre of
+    the distribution of A x.  Feasibility is not guaranteed by construction;
+    a found solution proves it."""
+    return [cornuejols_dawande(first_seed + 100 * m + D + i, m, D) for i in range(count)]
 
 
 def cd_batch(m: int, count: int, first_seed: int = 9000) -> List[Instance]:

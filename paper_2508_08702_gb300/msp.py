@@ -19,7 +19,7 @@ from . import build as _build
 MSP_OK, MSP_EINVAL, MSP_ENOMEM, MSP_ECUDA, MSP_EOVERFLOW, MSP_ERANK, MSP_ETIMEOUT, MSP_ETRUNC, \
     MSP_ESTATE, MSP_ECAP, MSP_EQUEUE = range(11)
 MSP_ALL, MSP_FIRST = 0, 1
-MSP_PLAIN, MSP_LEARNED, MSP_LDS = 0, 1, 2
+MSP_PLAIN, MSP_LEARNED, MSP_LDS, MSP_LDS_LEARNED = 0, 1, 2, 3
 MSP_HOST, MSP_DEVICE = 0, 1
 
 

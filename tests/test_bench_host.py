@@ -9,7 +9,7 @@ from paper_2508_08702_gb300 import instances as I
 
 
 def _instances(gen):
-    return I.cd_batch(8, 16) if gen == "cd8" else getattr(I, gen)()
+    return bench.make_instances(gen)
 
 
 @pytest.mark.parametrize("name", sorted(bench.WORKLOADS))
@@ -44,6 +44,21 @@ def test_baseline_sample_keeps_batch_order():
     assert [x.tag for x in sample] == [x.tag for x in batch if x.m <= 6 or (x.m == 7 and x.D >= 100)]
     assert any(x.m == 7 for x in sample)
     assert [x.tag for x in bench.cpu_sample(batch)] == [x.tag for x in batch if x.m <= 6]
+
+
+def test_oracle_rate_repeats_passes_to_the_minimum_time():
+    xs = [I.small(7200 + i, 3, 12, 20) for i in range(2)]
+    v, nodes, dt, runs = bench.oracle_nodes_per_s(xs, 60.0, lanes=8, min_seconds=0.2)
+    assert dt >= 0.2 and runs >= 2 and runs % 1 == 0
+    assert nodes > 0 and v == pytest.approx(nodes / dt)
+
+
+def test_headline_workloads_are_the_m12_rows():
+    for key, gen, cap, desc in bench.HEADLINE_FIRST:
+        xs = bench.make_instances(gen)
+        assert cap > 0
+        assert len(xs) == 4 and all(x.m == 12 and x.n == 110 for x in xs)
+        assert f"D={xs[0].D}" in desc
 
 
 def test_algorithmic_operation_count():
