@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--orders", default="plain,learned,lds,lds_learned",
                    help="first-solution workloads: orders to time")
     p.add_argument("--no-tune", action="store_true", help="batch64: library defaults instead of the autotuner")
+    p.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
+                   help="other workloads: set an msp_opts field (e.g. replicas=4, lds_rank=0)")
     p.add_argument("--no-headline", action="store_true",
                    help="batch64: skip the m=9 all-solutions and m=12 first-solution runs")
     return p.parse_args()
@@ -195,10 +197,13 @@ def extended(args):
     opts = dict(bkz_beta=bkz)
     if args.lanes:
         opts["lanes"] = args.lanes
+    for kv in args.opt:
+        k, v = kv.split("=", 1)
+        opts[k] = float(v) if "." in v else int(v)
     data = ("synthetic, centred right-hand side d = floor(sum a / 2), nothing planted" if insts[0].planted is None
             else "synthetic (planted instances of the paper's shapes)")
     out = {"workload": args.workload, "instances": len(insts), "m": insts[0].m, "n": insts[0].n, "D": insts[0].D,
-           "bkz_beta": bkz, "cap_s": cap, "data": data,
+           "bkz_beta": bkz, "cap_s": cap, "data": data, "opts": opts,
            "gpu": torch.cuda.get_device_name()}
     clocks = Clocks(torch.cuda.current_device())
     if mode == "all":
@@ -403,8 +408,11 @@ def launch_desc(opts, lanes):
 
 # the headline's paper configurations (synthetic stand-ins, seeds in instances.py)
 HEADLINE_FIRST = (
-    ("m12_n110_d100", "m12_n110", 30.0, "m=12, n=110, D=100, 4 planted instances (seeds 5000..5003)"),
-    ("m12_n110_d50_centred", ("centred", (12, 50)), 60.0,
+    # key, generator spec, runs (orders, cap in seconds, extra options), description
+    ("m12_n110_d100", "m12_n110", (("plain,learned,lds,lds_learned", 15.0, {}),),
+     "m=12, n=110, D=100, 4 planted instances (seeds 5000..5003)"),
+    ("m12_n110_d50_centred", ("centred", (12, 50)),
+     (("plain,learned", 30.0, {}), ("lds,lds_learned", 150.0, {"replicas": 4})),
      "m=12, n=110, D=50, 4 instances with the centred right-hand side (seeds 61250..61253): the paper's m=12 row"),
 )
 
@@ -414,7 +422,8 @@ def headline(args, clocks_index=0):
     rate: all solutions of the m = 9, n = 80, D = 100 batch (8 instances,
     BKZ-10; one warm-up on one m = 8 instance, which runs the same kernels),
     and the time to the first solution at m = 12 under the plain, learned and
-    limited-discrepancy orders (BKZ-10, a cap per run)."""
+    limited-discrepancy orders (BKZ-10, a cap per run; the discrepancy
+    searches run 4 shuffled replicas per instance, Sec. 4)."""
     from paper_2508_08702_gb300 import instances as I
     out = {}
     clocks = Clocks(clocks_index)
@@ -424,13 +433,16 @@ def headline(args, clocks_index=0):
     r["clocks"] = clocks.stop()
     r["workload"] = "m=9, n=80, D=100, 8 instances, planted x with 40 ones (seeds 4000..4007), BKZ-10, all solutions"
     out["m9_all"] = r
-    orders = args.orders.split(",")
-    theta, train_s = train_scorer() if any("learned" in o for o in orders) else (None, 0.0)
+    theta, train_s = train_scorer()
     first = {"scorer_training_s": train_s, "bkz_beta": 10, "workloads": {}}
     clocks.start()
-    for key, gen, cap, desc in HEADLINE_FIRST:
-        runs = run_first_solution(make_instances(gen), cap, orders, theta, bkz_beta=10)
-        first["workloads"][key] = {"workload": desc, "cap_s": cap, "orders": runs}
+    for key, gen, runs_spec, desc in HEADLINE_FIRST:
+        insts = make_instances(gen)
+        runs = {}
+        for orders, cap, extra in runs_spec:
+            for name, r in run_first_solution(insts, cap, orders.split(","), theta, bkz_beta=10, **extra).items():
+                runs[name] = dict(r, cap_s=cap, **extra)
+        first["workloads"][key] = {"workload": desc, "orders": runs}
     first["clocks"] = clocks.stop()
     out["first_solution"] = first
     return out

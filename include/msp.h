@@ -92,8 +92,8 @@ typedef struct {
                            /*     prefixes (0: 8 x the number of walkers / instances)     */
     int split_capacity;    /* [0] prefixes stored per instance (0: 4 x split_target)      */
     int warps_per_block;   /* [8] enumerator block size in warps                          */
-    int blocks_per_sm;     /* [0] enumerator blocks per SM (0: occupancy-derived)          */
-    int smem_tables;       /* [1] stage mu/bhat/B in shared memory when they fit           */
+    int blocks_per_sm;     /* [0] enumerator blocks per SM (0: as many as can be resident; */
+                           /*     larger values are capped at that)                     */
     int64_t sol_capacity;  /* [1<<20] solutions stored (over all instances)               */
     double max_seconds;    /* [600] safety cap on every enumeration's device time; the     */
                            /*       walkers stop and report MSP_ETIMEOUT when it passes   */

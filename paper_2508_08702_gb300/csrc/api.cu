@@ -293,7 +293,6 @@ void msp_default_opts(msp_opts* o) {
     o->split_capacity = 0;
     o->warps_per_block = 8;
     o->blocks_per_sm = 0;
-    o->smem_tables = 1;
     o->sol_capacity = 1 << 20;
     o->max_seconds = 600.0;
     o->donation_capacity = 1 << 16;

@@ -35,7 +35,7 @@ class msp_opts(C.Structure):
                 ("use_eps", C.c_int), ("lanes", C.c_int), ("split_depth", C.c_int),
                 ("split_target", C.c_int), ("split_capacity", C.c_int),
                 ("warps_per_block", C.c_int), ("blocks_per_sm", C.c_int),
-                ("smem_tables", C.c_int), ("sol_capacity", C.c_int64), ("max_seconds", C.c_double),
+                ("sol_capacity", C.c_int64), ("max_seconds", C.c_double),
                 ("donation_capacity", C.c_int64), ("log_features", C.c_int),
                 ("lds_budget", C.c_int), ("lds_max", C.c_int), ("first_split_target", C.c_int),
                 ("bkz_beta", C.c_int), ("bkz_max_tours", C.c_int), ("replicas", C.c_int),

@@ -54,9 +54,10 @@ def test_oracle_rate_repeats_passes_to_the_minimum_time():
 
 
 def test_headline_workloads_are_the_m12_rows():
-    for key, gen, cap, desc in bench.HEADLINE_FIRST:
+    for key, gen, runs, desc in bench.HEADLINE_FIRST:
         xs = bench.make_instances(gen)
-        assert cap > 0
+        for orders, cap, extra in runs:
+            assert cap > 0 and set(orders.split(",")) <= {"plain", "learned", "lds", "lds_learned"}
         assert len(xs) == 4 and all(x.m == 12 and x.n == 110 for x in xs)
         assert f"D={xs[0].D}" in desc
 
