@@ -37,7 +37,10 @@ METRIC = "enum nodes/s; time to all sols (m=9) & first sol (m=12), learned vs pl
 # the autotuner's grid for the batch (coordinate descent, library defaults first)
 TUNE_GRID = {"lanes": (8, 16), "warps_per_block": (8, 4), "blocks_per_sm": (0, 1),
              "split_target": (0, 256, 4096, 16384)}
-DRAM_BYTES_PER_NODE = (101.279488e6 + 322.009600e6) / 268321291   # enum_kernel<8, 8, 0>, ncu
+DRAM_BYTES_PER_NODE = (105.400064e6 + 323.852544e6) / 268321291   # enum_kernel<8, 8, 0>, ncu
+# FP64 lane operations the same capture executed, per evaluated node (ncu
+# sm__sass_thread_inst_executed_op_fp64_pred_on): the counter-based FP64 work
+FP64_LANE_OPS_PER_NODE = 10288881548 / 268321291
 UNIT = "nodes/s"
 WORKLOAD = "batch of 64 fMSP instances, m~U{4..7}, n=10(m-1), D in {50,100,200}, all solutions"
 
@@ -639,8 +642,14 @@ def main():
     traffic = None
     if lanes == 8:
         traffic = DRAM_BYTES_PER_NODE * res.total["nodes"]
+    counted = FP64_LANE_OPS_PER_NODE * (res.total["nodes"] - sum(s["split_nodes"] for s in res.stats))
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_dfma / 1e9,
             "unit": "Gop/s (FP64 lane ops)", "frac": achieved / peak_dfma, "traffic": traffic,
+            "frac_kind": "FP64-equivalent: the method's algorithmic FP64 operations per launch over the FP64 FMA "
+                         "peak; most of them run as exact int64 fixed-point arithmetic",
+            "fp64_counted_frac": (counted / (ph["enumerate"] / 1e3)) / peak_dfma if lanes == 8 else None,
+            "fp64_counted_source": "FP64 lane instructions per node from ncu (profiles/enum_kernel_batch4.md) x "
+                                   "this launch's nodes / enumeration time / peak",
             "traffic_source": "ncu dram bytes per node of a 4-instance capture, scaled by nodes",
             "peak_source": "measured FP64 fma throughput (msp_fp64_peak) on this GPU; the nominal "
                            "GB300 FP64 rate 1.25 TFLOP/s is 625 G fma/s"}
