@@ -25,7 +25,7 @@ __global__ void permute_kernel(Pools P, int32_t* perm, int32_t* rperm, unsigned 
 cudaError_t launch_split(const Pools& P, const EnumCfg& cfg, int lanes, int max_depth, int64_t target,
                          int64_t* fcnt, cudaStream_t st);
 cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
-                        int Kmax, int dimPad, bool extended, cudaStream_t st);
+                        int Kmax, int dimPad, int variant, cudaStream_t st);
 cudaError_t launch_collect(const Pools& P, int64_t* soff, unsigned long long* fill, SolRec* seg, SolRec* out,
                            cudaStream_t st);
 cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, int keep, cudaStream_t st);
@@ -653,8 +653,10 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
         Pq.qperm = ptr<int64_t>(c->perm);
     }
     if (!cont) record(c, c->evs1);
+    // walker variant: general bounds, binary discrepancy search, or plain
+    const int variant = c->bounded ? 2 : (lds >= 0 ? 1 : 0);
     if ((e = launch_enum(Pq, cfg, c->lanes, blocks, threads, ptr<char>(c->scratch), c->Kmax, c->dimPad,
-                         c->bounded || lds >= 0, c->st)) !=
+                         variant, c->st)) !=
         cudaSuccess)
         return cuda_fail(c, e, "enumerate");
     ++c->launches;

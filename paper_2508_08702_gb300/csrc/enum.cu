@@ -344,6 +344,15 @@ __device__ __forceinline__ unsigned group_mask() {
     return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
 }
 
+// sum of a per-lane counter over the lanes of a group (every lane gets it)
+template <int G>
+__device__ __forceinline__ unsigned long long group_sum(unsigned v, unsigned gmask) {
+    unsigned long long s = v;
+#pragma unroll
+    for (int off = G / 2; off >= 1; off >>= 1) s += __shfl_xor_sync(gmask, s, off, G);
+    return s;
+}
+
 // exact int -> double without the FP64 pipe (|v| < 2^31)
 __device__ __forceinline__ double i2d_exact(int v) {
     if (v == 0) return 0.0;
@@ -727,13 +736,17 @@ enum : int { kFetch = 0, kWalk = 1, kDone = 2 };
 #define MSP_ENUM_MIN_BLOCKS(g) ((g) >= 8 ? 2 : 1)
 #endif
 
-// EXT: the extended walker -- the batch holds an instance with bounds beyond
-// 0/1 (r_max > 1) or the search is a limited-discrepancy iteration.  The
-// plain variant (binary, depth-first) keeps r_max = 1 and carries no
-// discrepancy bookkeeping, so its register budget stays with the hot loop.
-template <int G, int CPL, bool EXT>
+// Variants V of the walker: 0 plain (binary bounds, depth-first), 1 binary
+// with the discrepancy bookkeeping of a limited-discrepancy iteration, 2
+// general bounds (r_max >= 1; depth-first or discrepancy search).  EXT: the
+// discrepancy bookkeeping is compiled in; BND: r_max is a run-time value and
+// leaves take the general check.  Each variant carries only the state it
+// needs, so the register budget stays with the hot loop.
+template <int G, int CPL, int V>
 __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     enum_kernel(Pools P, EnumCfg cfg, char* scratch, WalkerLayout WL) {
+    constexpr bool EXT = V != 0;
+    constexpr bool BND = V == 2;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lg = threadIdx.x & (G - 1);
     const unsigned gmask = group_mask<G>();
@@ -879,7 +892,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 Btab = P.B + I.offB;
                 bqtab = P.bq + I.offBq;
                 nbqtab = P.nbq + I.offNbq;
-                if (EXT) rmax = I.rmax;
+                if (BND) rmax = I.rmax;
                 {
                     const double R = bound_R(I);
                     eps = slack_of(R, cfg.use_eps);
@@ -958,20 +971,43 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
             bool abort = false, quiet = false;
             __syncwarp(gmask);   // level state written by lane 0 in the previous step
             if (act == kEnter) {
-                // entering level t: centre by the cached fold, start of the zig-zag
-                const int Jt = L.J(t);
-                double* srow = sigma + (int64_t)t * (Kmax + 1);
-                double acc = (Jt + 1 < dd) ? srow[Jt + 1] : 0.0;
-                for (int i = Jt; i > t; --i) {
-                    acc = __fma_rn(L.ud(i), muT[(int64_t)t * dd + i], acc);
-                    srow[i] = acc;
+                // Entering level t: the centre y_t by the cached fold, and the
+                // start of the zig-zag.  Lane 0 folds level t's cache row from
+                // its highest changed index Jt down to t + 1.  Lane l > 0 takes
+                // the row of level t - l, whose pending indices are those of
+                // the levels from t down to t - l (Q); when they all lie in
+                // Jt .. t + 1 it folds that row over the same indices alongside
+                // lane 0 (the u above t are fixed from here on), so entering
+                // level t - l later folds only the indices added below t.  A
+                // lane whose row has older changes above Jt keeps them pending
+                // (J = Q) for later.  Every row is the same fold in the same
+                // order as without the lanes' help, so every y_t is bit for
+                // bit the same.
+                const int tl = t - lg;                     // this lane's level
+                int Q = (tl >= 0) ? (int)L.J(tl) : -1;
+#pragma unroll
+                for (int off = 1; off < G; off <<= 1) {
+                    const int v = __shfl_up_sync(gmask, Q, off, G);
+                    if (lg >= off) Q = max(Q, v);
                 }
-                y = acc;
-                cfma += (unsigned)(Jt - t);
-                if (lg == 0) {
-                    if (t > 0 && L.J(t - 1) < max(Jt, t)) L.J(t - 1) = (unsigned char)max(Jt, t);
-                    L.J(t) = (unsigned char)t;
+                const int Jt = __shfl_sync(gmask, Q, 0, G);
+                const bool fold = tl >= 0 && Q <= Jt;
+                double acc = 0.0;
+                if (fold) {
+                    double* srow = sigma + (int64_t)tl * (Kmax + 1);
+                    const double* mrow = muT + (int64_t)tl * dd;
+                    acc = (Q + 1 < dd) ? srow[Q + 1] : 0.0;
+                    for (int i = Q; i > t; --i) {
+                        acc = __fma_rn(L.ud(i), mrow[i], acc);
+                        srow[i] = acc;
+                    }
+                    if (Q > t) cfma += (unsigned)(Q - t);
                 }
+                y = __shfl_sync(gmask, acc, 0, G);
+                __syncwarp(gmask);
+                if (tl >= 0) L.J(tl) = (unsigned char)(fold ? t : Q);   // rows valid above index J
+                // the level below the lanes' reach inherits the pending index
+                if (lg == G - 1 && fold && tl > 0 && L.J(tl - 1) < Q) L.J(tl - 1) = (unsigned char)Q;
                 if (centre_round(y, u1, s)) { abort = true; u1 = 0; s = 1; }
                 onedir = false; dir = 0; zi = 1;
                 if (zp && cfg.sym) { u1 = 0; onedir = true; dir = 1; }
@@ -1009,12 +1045,13 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                               EXT ? cfg.lds : -1, cfg.lds_rank, gmask);
                 // the 32-bit walk counters are flushed long before they could wrap
                 // (at most 1024 nodes and 1024 x 128 centre fmas between checks)
-                if (nodes >= (1u << 30) || cfma >= (1u << 30)) {
+                if (nodes >= (1u << 30) || __any_sync(gmask, cfma >= (1u << 30))) {
+                    const unsigned long long csum = group_sum<G>(cfma, gmask);
                     if (lg == 0) {
                         atomicAdd(&P.cnt[inst].nodes, (unsigned long long)nodes);
                         atomicAdd(&P.cnt[inst].passed, (unsigned long long)passed);
                         atomicAdd(&P.cnt[inst].leaves, (unsigned long long)leaves);
-                        atomicAdd(&P.cnt[inst].center_fma, (unsigned long long)cfma);
+                        atomicAdd(&P.cnt[inst].center_fma, csum);
                         atomicAdd(&P.cnt[inst].fallbacks, (unsigned long long)fallbacks);
                         if (cuts) atomicAdd(&P.cnt[inst].lds_cuts, (unsigned long long)cuts);
                         atomicAdd(reinterpret_cast<unsigned long long*>(&P.plog_nodes[L.gid()]),
@@ -1047,7 +1084,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     if (t == 0) {
                         ++leaves;
                         if (!EXT || cfg.lds < 0 || dab + cost == cfg.lds)
-                            item_sols += EXT ? leaf_check_bounded<G, CPL>(P, cfg, inst, L, u, gmask)
+                            item_sols += BND ? leaf_check_bounded<G, CPL>(P, cfg, inst, L, u, gmask)
                                              : leaf_check<G, CPL>(P, cfg, inst, L, u, gmask);
                         act = kNext;
                     } else {
@@ -1068,7 +1105,7 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                             // r_max ||w||_1 (Theorem 2 with r_max); r_max = 1 for binary problems
                             long long Lfix = (long long)lsum << kHiShift;
                             long long Ebase = Ech + (Ech >> 10) + ((long long)ehalf << kHiShift);
-                            if (EXT && rmax != 1) { Lfix *= rmax; Ebase *= rmax; }
+                            if (BND && rmax != 1) { Lfix *= rmax; Ebase *= rmax; }
                             const long long M = fix_trunc(rho, Sf) - Lfix - eps_fix;
                             const long long Etot = Ebase + (Lfix >> 32) + 64;
                             if (M > Etot) fail = true;
@@ -1187,12 +1224,13 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 }
             }
             if (finished) {
+                const unsigned long long csum = group_sum<G>(cfma, gmask);
                 if (lg == 0) {
                     if (abort && !quiet && !(*(volatile unsigned*)&ctrl->stop)) set_status(P.inst[inst], ST_EOVERFLOW);
                     atomicAdd(&P.cnt[inst].nodes, (unsigned long long)nodes);
                     atomicAdd(&P.cnt[inst].passed, (unsigned long long)passed);
                     atomicAdd(&P.cnt[inst].leaves, (unsigned long long)leaves);
-                    atomicAdd(&P.cnt[inst].center_fma, (unsigned long long)cfma);
+                    atomicAdd(&P.cnt[inst].center_fma, csum);
                     atomicAdd(&P.cnt[inst].fallbacks, (unsigned long long)fallbacks);
                     if (cuts) atomicAdd(&P.cnt[inst].lds_cuts, (unsigned long long)cuts);
                     atomicAdd(reinterpret_cast<unsigned long long*>(&P.plog_nodes[L.gid()]), (unsigned long long)nodes);
@@ -1313,9 +1351,9 @@ int enum_blocks_per_sm(int lanes, int threads, int dimMax, int Kmax) {
     const int smem = enum_smem_bytes(lanes, threads, Kmax);
 #define MSP_OCC(g, c)                                                                                 \
     if (lanes == g && cpl == c) {                                                                     \
-        if (cudaFuncSetAttribute(enum_kernel<g, c, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) \
+        if (cudaFuncSetAttribute(enum_kernel<g, c, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) \
                 != cudaSuccess ||                                                                     \
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<g, c, false>, threads, smem) !=     \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<g, c, 0>, threads, smem) !=     \
                 cudaSuccess) {                                                                        \
             cudaGetLastError();                                                                       \
             n = 0;                                                                                    \
@@ -1331,7 +1369,7 @@ int64_t walker_bytes(int Kmax, int dimPad) { return WalkerLayout{Kmax, dimPad}.b
 int64_t donation_slot_bytes(int Kmax, int dimPad) { return donation_stride(Kmax, dimPad); }
 
 cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
-                        int Kmax, int dimPad, bool extended, cudaStream_t st) {
+                        int Kmax, int dimPad, int variant, cudaStream_t st) {
     WalkerLayout W{Kmax, dimPad};
     const int cpl = pick_cpl(lanes, P.dimMax);
     const int smem = enum_smem_bytes(lanes, threads, Kmax);
@@ -1349,8 +1387,9 @@ cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int block
     }
 #define MSP_LAUNCH(g, c)                                                                              \
     if (lanes == g && cpl == c) {                                                                     \
-        if (extended) MSP_LAUNCH1(g, c, true)                                                         \
-        else MSP_LAUNCH1(g, c, false)                                                                 \
+        if (variant == 2) MSP_LAUNCH1(g, c, 2)                                                        \
+        else if (variant == 1) MSP_LAUNCH1(g, c, 1)                                                   \
+        else MSP_LAUNCH1(g, c, 0)                                                                     \
     }
     MSP_ENUM_SHAPES(MSP_LAUNCH)
 #undef MSP_LAUNCH

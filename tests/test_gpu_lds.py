@@ -109,3 +109,33 @@ def test_lds_time_cap_and_order_errors():
     with pytest.raises(M().MspError):
         ctx.msp_run_async(M().MSP_FIRST, M().MSP_LDS)
     ctx.close()
+
+
+@pytest.mark.parametrize("k", [1, 4])
+def test_learned_order_inside_an_iteration_changes_no_node(k):
+    """MSP_LDS_LEARNED takes an iteration's subtrees in the scorer's order:
+    the same nodes, leaves and solutions as the oracle's iteration."""
+    from oracle import mlp as R
+    res, sols, ctx = M().solve(MIXED, order=M().MSP_LDS_LEARNED, scorer=R.init(9), lds_budget=k, lanes=8,
+                               split_depth=8, max_seconds=120.0)
+    for i, inst in enumerate(MIXED):
+        ref = _oracle(inst, lds=k)
+        st = res.stats[i]
+        assert (st["nodes"], st["passed"], st["leaves"]) == (ref.nodes, ref.passed, ref.leaves), i
+        assert np.array_equal(sols[i], ref.solutions), i
+    ctx.close()
+
+
+def test_learned_order_inside_the_search_finds_the_same_first_budget():
+    from oracle import mlp as R
+    insts = [x for x in I.batch_m4_7(24) if x.m <= 6][:8]
+    res, sols, ctx = M().solve(insts, mode=M().MSP_FIRST, order=M().MSP_LDS_LEARNED, scorer=R.init(4), lanes=8,
+                               max_seconds=120.0)
+    for i, inst in enumerate(insts):
+        _, kern, g = O.reduce(inst.A, inst.d)
+        its = O.enumerate_lds(kern, g, inst.A, inst.d, lanes=8, first=True)
+        assert res.stats[i]["lds_budget"] == len(its) - 1, i
+        assert len(sols[i]) >= 1
+        for x in sols[i].astype(np.int64):
+            assert np.array_equal(inst.A.astype(np.int64) @ x, inst.d)
+    ctx.close()
