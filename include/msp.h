@@ -127,6 +127,18 @@ typedef struct {
                            /*     p in its level's walk (p = 0 for the rounded centre),  */
                            /*     0: one for every value after the first (Sec. 3 calls  */
                            /*     a discrepancy a deviation from the heuristic order)    */
+    int fuse;              /* [0] 1: msp_run_async / msp_graph_capture of an all-        */
+                           /*     solutions, depth-first, binary step reduce, split and   */
+                           /*     enumerate in one cooperative launch -- the blocks       */
+                           /*     prepare the instances (LLL, tables, split) and walkers  */
+                           /*     start on each instance as soon as it is published, so  */
+                           /*     the slowest reductions overlap the enumeration of the  */
+                           /*     others.  Same nodes and solutions as 0 (separate        */
+                           /*     launches); msp_phase_ms then reports the reduction and  */
+                           /*     split as 0 and the whole launch as the enumeration.     */
+                           /*     Off by default: on GB300 the fused walker is slower    */
+                           /*     than the overlap gains (605 against 522 ms per step of */
+                           /*     the 64-instance batch)                                  */
 } msp_opts;
 
 /* Per-instance results of an enumeration. */

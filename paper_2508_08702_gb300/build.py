@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmsp_gb300.so")
 ROOT = os.path.dirname(HERE)
 SOURCES = ["api.cu", "lattice.cu", "enum.cu", "learn.cu", "mlp.cu", "peak.cu", "noalloc.cu"]
-HEADERS = ["common.cuh"]
+HEADERS = ["common.cuh", "reduce.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr"]

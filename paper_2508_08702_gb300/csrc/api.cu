@@ -25,14 +25,14 @@ __global__ void permute_kernel(Pools P, int32_t* perm, int32_t* rperm, unsigned 
 cudaError_t launch_split(const Pools& P, const EnumCfg& cfg, int lanes, int max_depth, int64_t target,
                          int64_t* fcnt, cudaStream_t st);
 cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
-                        int Kmax, int dimPad, int variant, cudaStream_t st);
+                        int Kmax, int dimPad, int variant, const Pipe& pipe, cudaStream_t st);
 cudaError_t launch_collect(const Pools& P, int64_t* soff, unsigned long long* fill, SolRec* seg, SolRec* out,
                            cudaStream_t st);
 cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, int keep, cudaStream_t st);
 cudaError_t launch_ring_init(unsigned long long* seq, int64_t cap, cudaStream_t st);
 int64_t walker_bytes(int Kmax, int dimPad);
 int64_t donation_slot_bytes(int Kmax, int dimPad);
-int enum_blocks_per_sm(int lanes, int threads, int dimMax, int Kmax);
+int enum_blocks_per_sm(int lanes, int threads, int dimMax, int Kmax, int variant);
 int enum_smem_bytes(int lanes, int threads, int Kmax);
 cudaError_t launch_features(const Pools& P, float* prof, float* feat, int sms, cudaStream_t st);
 cudaError_t launch_order(const Pools& P, const float* y, int64_t npad, unsigned long long* keys,
@@ -86,7 +86,7 @@ struct msp_ctx {
     // device buffers
     Buf inst, cnt, A, d, basis, gram, mu, Bl, kb, muT, B, bhat, bq, nbq, fu, fdisc, fxsum, frho, fw, fcnt, qbase, sols, ctrl, soff,
         fill, seg, sout, scratch, plog_nodes, plog_sols, don, don_seq, feat, prof, yout, skeys, svals, skeys2,
-        svals2, perm, theta, mlpwork, inst0, skip, bkzs, rb, gsolved, gfirst, colperm;
+        svals2, perm, theta, mlpwork, inst0, skip, bkzs, rb, gsolved, gfirst, colperm, rl;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cst = nullptr;          // private stream the step is captured on
@@ -96,6 +96,7 @@ struct msp_ctx {
     std::vector<InstDesc> graph_inst;
     std::vector<int32_t> lds_done;       // per instance: budget that solved / finished it (-1)
     bool last_lds = false;
+    bool last_fused = false;             // the last enumeration also reduced and split (one launch)
     bool scorer_set = false;
     bool features_valid = false;
     std::vector<int64_t> soff_h;
@@ -210,7 +211,12 @@ void enum_launch_shape(const msp_ctx* c, int* blocks, int* threads) {
     // blocks per SM: the option, at most as many as can be resident (the
     // walkers are persistent: a block that cannot start would only start
     // once others have finished)
-    const int fit = std::max(1, enum_blocks_per_sm(c->lanes, t, c->dimMax, c->Kmax));
+    // (the fused launch's variant counts too, so both launches have the same
+    // walkers: its blocks must all be resident at once)
+    int fit = enum_blocks_per_sm(c->lanes, t, c->dimMax, c->Kmax, 0);
+    const int fit3 = enum_blocks_per_sm(c->lanes, t, c->dimMax, c->Kmax, 3);
+    if (fit3 > 0) fit = std::min(fit, fit3);
+    fit = std::max(1, fit);
     int bps = c->o.blocks_per_sm;
     bps = bps <= 0 ? fit : std::min(bps, fit);
     *blocks = c->sms * bps;
@@ -219,6 +225,7 @@ void enum_launch_shape(const msp_ctx* c, int* blocks, int* threads) {
 // Buffers whose size follows the per-instance frontier capacity F (prefixes,
 // their logs and features, the sort keys of the queue order).  Grow-only.
 msp_status size_frontier(msp_ctx* c, int64_t F) {
+    F = (F + 31) / 32 * 32;   // every instance's frontier region on its own 128-byte lines
     const size_t n = (size_t)c->count, K = (size_t)c->Kmax, D = (size_t)c->dimPad;
     const int64_t cap = (int64_t)n * F;
     int64_t npad = 1;
@@ -300,6 +307,7 @@ void msp_default_opts(msp_opts* o) {
     o->lds_budget = -1;
     o->lds_max = 127;
     o->lds_rank = 1;
+    o->fuse = 0;
     o->first_split_target = 16384;
     o->bkz_beta = 0;
     o->bkz_max_tours = 16;
@@ -372,7 +380,7 @@ void msp_destroy(msp_ctx* c) {
                   &c->fill, &c->seg, &c->sout, &c->scratch, &c->plog_nodes, &c->plog_sols, &c->don,
                   &c->don_seq, &c->feat, &c->prof, &c->yout, &c->skeys, &c->svals, &c->skeys2, &c->svals2,
                   &c->perm, &c->theta, &c->mlpwork, &c->inst0, &c->skip, &c->bkzs, &c->rb, &c->gsolved,
-                  &c->gfirst, &c->colperm};
+                  &c->gfirst, &c->colperm, &c->rl};
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->cst) cudaStreamDestroy(c->cst);
@@ -442,9 +450,10 @@ msp_status msp_build_lattice_bounds(msp_ctx* c, int count, const int32_t* dims, 
             I.offBasis = nBasis; nBasis += (int64_t)I.K * I.L;
             I.offGram = nGram; nGram += (int64_t)I.K * I.K;
             I.offMu = nMu; nMu += (int64_t)2 * I.K * I.K + I.K;
-            I.offBl = nK; I.offB = nK; nK += I.K;
-            I.offKb = nKb; I.offBhat = nKb; nKb += (int64_t)I.K * I.dim;
-            I.offMuT = nT; nT += (int64_t)I.K * I.K;
+            // (128-byte aligned regions, see InstDesc: 16 doubles, 32 int32)
+            I.offBl = nK; I.offB = nK; nK += (I.K + 15) / 16 * 16;
+            I.offKb = nKb; I.offBhat = nKb; nKb += ((int64_t)I.K * I.dim + 31) / 32 * 32;
+            I.offMuT = nT; nT += ((int64_t)I.K * I.K + 15) / 16 * 16;
             Kmax = std::max(Kmax, I.K);
             dimMax = std::max(dimMax, I.dim);
         }
@@ -464,7 +473,7 @@ msp_status msp_build_lattice_bounds(msp_ctx* c, int count, const int32_t* dims, 
     int64_t nBq = 0;
     for (int i = 0; i < count; ++i) {
         h[i].offBq = nBq;
-        h[i].offNbq = (int64_t)i * Kmax;
+        h[i].offNbq = (int64_t)i * ((Kmax + 15) / 16 * 16);
         nBq += (int64_t)h[i].K * c->dimPad;
     }
     // split sizes
@@ -491,7 +500,7 @@ msp_status msp_build_lattice_bounds(msp_ctx* c, int count, const int32_t* dims, 
     ENSURE(B, sizeof(double) * nK);
     ENSURE(bhat, sizeof(double) * nKb);
     ENSURE(bq, sizeof(int32_t) * nBq);
-    ENSURE(nbq, sizeof(int64_t) * (size_t)count * Kmax);
+    ENSURE(nbq, sizeof(int64_t) * (size_t)count * ((Kmax + 15) / 16 * 16));
     ENSURE(don, (size_t)c->o.donation_capacity * donation_slot_bytes(Kmax, c->dimPad));
     ENSURE(don_seq, sizeof(unsigned long long) * (size_t)std::max<int64_t>(c->o.donation_capacity, 1));
     ENSURE(qbase, sizeof(int64_t) * (count + 1));
@@ -589,11 +598,21 @@ msp_status msp_reduce(msp_ctx* c) {
     return MSP_OK;
 }
 
+// A whole step can run as one fused launch (reduction and split inside the
+// enumeration kernel) when the queue needs no global order: all solutions,
+// depth-first, no feature log, binary bounds.
+static bool fusable(const msp_ctx* c, int mode, int order) {
+    if (!(c->o.fuse && mode == MSP_ALL && order == MSP_PLAIN && !c->o.log_features && !c->bounded)) return false;
+    int blocks, threads;
+    enum_launch_shape(c, &blocks, &threads);
+    return enum_blocks_per_sm(c->lanes, threads, c->dimMax, c->Kmax, 3) * c->sms >= blocks;
+}
+
 // Queues one enumeration.  lds >= 0: one limited-discrepancy iteration with
 // that budget; cont: a later iteration of the same search (counters, stored
 // solutions, start time and deadline carry over).
 static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_cap_s, int lds = -1,
-                                  bool cont = false) {
+                                  bool cont = false, bool fused = false) {
     EnumCfg cfg{c->o.hoelder, c->o.sym, c->o.use_eps, mode == MSP_FIRST ? 1 : 0, lds, c->o.lds_rank};
     int blocks, threads;
     enum_launch_shape(c, &blocks, &threads);
@@ -612,16 +631,48 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
     // the caller's cap, else the context's safety cap: no walk outlives it
     const double cap_s = time_cap_s > 0 ? std::min(time_cap_s, c->o.max_seconds) : c->o.max_seconds;
     const unsigned long long cap_ns = (unsigned long long)(cap_s * 1e9);
+    Pipe pipe{};
+    if (fused) {   // the reduction and the split run inside the enumeration launch
+        if ((s = ensure(c, c->rl, sizeof(int64_t) * 3 * (size_t)c->count, "publish list")) != MSP_OK) return s;
+        // ready flags of the publish list start at zero
+        if ((e = cudaMemsetAsync(ptr<int64_t>(c->rl) + 2 * (size_t)c->count, 0, sizeof(int64_t) * (size_t)c->count,
+                                 c->st)) != cudaSuccess)
+            return cuda_fail(c, e, "publish list");
+        pipe.on = 1;
+        pipe.delta = c->o.delta;
+        pipe.eta = c->o.eta;
+        pipe.lll_max_iter = c->o.lll_max_iter;
+        pipe.max_ns = (unsigned long long)(c->o.max_seconds * 1e9);
+        pipe.bkz_beta = c->o.bkz_beta;
+        pipe.bkz_max_tours = c->o.bkz_max_tours;
+        if (c->o.bkz_beta >= 2) {
+            BkzScratch S{nullptr, BkzScratch::bytes(c->Kmax, c->dimMax), c->Kmax, c->dimMax};
+            if ((s = ensure(c, c->bkzs, (size_t)S.stride * c->count, "bkz scratch")) != MSP_OK) return s;
+            S.base = ptr<char>(c->bkzs);
+            pipe.S = S;
+        }
+        pipe.use_eps = c->o.use_eps;
+        pipe.dimPad = c->dimPad;
+        pipe.split_depth = c->o.split_depth;
+        pipe.split_target = target;
+        pipe.fcnt = ptr<int64_t>(c->fcnt);
+        pipe.rl = ptr<int64_t>(c->rl);
+        record(c, c->evr0);   // (reduction and split: inside the enumeration's time)
+        record(c, c->evr1);
+        c->reduce_timed = true;
+    }
     if (!cont) record(c, c->ev0);
     if ((e = launch_start(ptr<Ctrl>(c->ctrl), cap_ns, cont ? 1 : 0, c->st)) != cudaSuccess)
         return cuda_fail(c, e, "start");
     ++c->launches;
     Pools Ps = c->P;
     Ps.skip = lds >= 0 ? ptr<unsigned char>(c->skip) : nullptr;
-    if ((e = launch_split(Ps, cfg, c->lanes, c->o.split_depth, target, ptr<int64_t>(c->fcnt), c->st)) !=
-        cudaSuccess)
-        return cuda_fail(c, e, "split");
-    c->launches += 2;
+    if (!fused) {
+        if ((e = launch_split(Ps, cfg, c->lanes, c->o.split_depth, target, ptr<int64_t>(c->fcnt), c->st)) !=
+            cudaSuccess)
+            return cuda_fail(c, e, "split");
+        c->launches += 2;
+    }
     // subtree features and queue order: the first-solution mode interleaves the
     // instances by rank (depth-first rank, or the scorer's rank when learned)
     const bool learned = (order == MSP_LEARNED || order == MSP_LDS_LEARNED) && c->scorer_set;
@@ -654,9 +705,9 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
     }
     if (!cont) record(c, c->evs1);
     // walker variant: general bounds, binary discrepancy search, or plain
-    const int variant = c->bounded ? 2 : (lds >= 0 ? 1 : 0);
+    const int variant = fused ? 3 : (c->bounded ? 2 : (lds >= 0 ? 1 : 0));
     if ((e = launch_enum(Pq, cfg, c->lanes, blocks, threads, ptr<char>(c->scratch), c->Kmax, c->dimPad,
-                         variant, c->st)) !=
+                         variant, pipe, c->st)) !=
         cudaSuccess)
         return cuda_fail(c, e, "enumerate");
     ++c->launches;
@@ -668,6 +719,7 @@ static msp_status queue_enumerate(msp_ctx* c, int mode, int order, double time_c
     record(c, c->ev1);
     c->last_mode = mode;
     c->last_lds = lds >= 0;
+    c->last_fused = fused;
     c->state = 3;
     c->sout_valid = false;
     return MSP_OK;
@@ -729,6 +781,7 @@ msp_status msp_run_async(msp_ctx* c, int mode, int order) {
     if (mode != MSP_ALL && mode != MSP_FIRST) return fail(c, MSP_EINVAL, "bad mode");
     if (order != MSP_PLAIN && order != MSP_LEARNED)
         return fail(c, MSP_EINVAL, "msp_run_async: order must be MSP_PLAIN or MSP_LEARNED (MSP_LDS: msp_enumerate)");
+    if (fusable(c, mode, order)) return queue_enumerate(c, mode, order, 0.0, -1, false, true);
     msp_status s = msp_reduce(c);
     if (s != MSP_OK) return s;
     return queue_enumerate(c, mode, order, 0.0);
@@ -744,6 +797,7 @@ static msp_status queue_step(msp_ctx* c, int mode, int order) {
     ++c->launches;
     msp_status s = check_launch(c, "build_lattice_kernel");
     if (s != MSP_OK) return s;
+    if (fusable(c, mode, order)) return queue_enumerate(c, mode, order, 0.0, -1, false, true);
     if ((s = msp_reduce(c)) != MSP_OK) return s;
     return queue_enumerate(c, mode, order, 0.0);
 }

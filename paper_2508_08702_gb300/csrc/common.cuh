@@ -18,8 +18,12 @@ enum : int32_t {
 };
 
 // Descriptor of one instance of a batch; offsets are element offsets into
-// the pools of Pools below.
-struct InstDesc {
+// the pools of Pools below.  Descriptors, and every per-instance region of
+// the tables the walkers read, start on their own 128-byte lines: in the
+// fused launch an instance is prepared while walkers on other SMs already
+// read the tables of others, and a line shared by two instances could sit
+// in an SM's L1 with the bytes of the one not yet prepared.
+struct __align__(128) InstDesc {
     int32_t m, n, K, L;      // K = n + 1 basis vectors of length L = m + n + 1
     int32_t dd, dim;         // kernel rank (set by the extractor), dim = n + 1
     int32_t status;
@@ -129,6 +133,8 @@ struct Ctrl {
     unsigned long long start_ns;       // globaltimer at the start of the enumeration
     int solved;                        // first-solution mode: instances with a solution
     int active;                        // instances with subtrees to enumerate
+    // fused launch: instances join the queue as their blocks finish them
+    unsigned long long qres;           // reservations: (instances << 40) | queue positions reserved
 };
 
 // Enumeration options passed to the split and enumeration kernels.
@@ -145,6 +151,26 @@ struct BkzScratch {
         const int64_t raw = 8 * (2 * K * D + 3 * K * K + 5 * K) + 4 * 5 * K;
         return (raw + 255) / 256 * 256;
     }
+};
+
+// Fused launch: the enumeration kernel's blocks first prepare the instances
+// of the batch (block b takes instances b, b + grid, ...: warp 0 reduces the
+// lattice and builds the tables, then the whole block splits the top levels)
+// and publish each one's subtrees to the queue; the walkers start on the
+// published subtrees while other instances are still being prepared.
+struct Pipe {
+    int on;                            // 0: the instances were prepared by earlier launches
+    double delta, eta;                 // LLL parameters
+    int64_t lll_max_iter;
+    unsigned long long max_ns;         // device-time cap of one reduction
+    int bkz_beta, bkz_max_tours;       // BKZ of the kernel basis (beta < 2: none)
+    BkzScratch S;
+    int use_eps, dimPad;
+    int split_depth;
+    int64_t split_target;
+    int64_t* fcnt;                     // split scratch (per instance, F entries)
+    int64_t* rl;                       // publish list: [count] queue bases, [count] instances,
+                                       // [count] ready flags (zeroed before the launch)
 };
 
 struct EnumCfg {

@@ -30,6 +30,7 @@
 // only the changed tail of the fold is redone -- the same operations in
 // the same order as the full fold.
 #include "common.cuh"
+#include "reduce.cuh"
 
 namespace msp {
 
@@ -168,10 +169,10 @@ __device__ int64_t block_exclusive_scan(int64_t* cnt, int64_t n) {
     return total;
 }
 
+// The split of one instance by a whole block (any number of threads).
 template <int G>
-__global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int max_depth, int64_t target,
-                                                    int64_t* fcnt) {
-    const int inst = blockIdx.x;
+__device__ __noinline__ void split_inst(const Pools& P, const EnumCfg& cfg, int inst, int max_depth, int64_t target,
+                                        int64_t* fcnt) {
     InstDesc& I = P.inst[inst];
     __shared__ int s_ok;
     if (threadIdx.x == 0) s_ok = (I.status == ST_OK) && !(P.skip && P.skip[inst]);
@@ -238,6 +239,12 @@ __global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int ma
     if (ovf) set_status(I, ST_EOVERFLOW);
 }
 
+template <int G>
+__global__ void __launch_bounds__(256) split_kernel(Pools P, EnumCfg cfg, int max_depth, int64_t target,
+                                                    int64_t* fcnt) {
+    split_inst<G>(P, cfg, blockIdx.x, max_depth, target, fcnt);
+}
+
 // resets the control words and arms the time cap on the device clock;
 // keep != 0 continues a search (the next limited-discrepancy iteration): the
 // start time, the deadline and the stored solutions carry over
@@ -259,6 +266,7 @@ __global__ void start_kernel(Ctrl* c, unsigned long long cap_ns, int keep) {
     }
     c->solved = 0;
     c->active = 0;
+    c->qres = 0;
 }
 
 // exclusive prefix sums of the per-instance prefix counts (one thread)
@@ -313,9 +321,13 @@ struct Levels {
     __device__ __forceinline__ unsigned char& pos(int t) const { return base[37 * K + t]; }
     // the queue item (prefix) of the current walk
     __device__ __forceinline__ int64_t& gid() const { return *reinterpret_cast<int64_t*>(base + (38 * K + 7) / 8 * 8); }
+    // fused launch: the queue position taken but not yet published (-1: none)
+    __device__ __forceinline__ int64_t& ticket() const {
+        return *reinterpret_cast<int64_t*>(base + (38 * K + 7) / 8 * 8 + 8);
+    }
 };
 
-__host__ __device__ inline int level_bytes(int Kmax) { return ((38 * Kmax + 7) / 8 * 8 + 8 + 15) / 16 * 16; }
+__host__ __device__ inline int level_bytes(int Kmax) { return ((38 * Kmax + 7) / 8 * 8 + 16 + 15) / 16 * 16; }
 
 __device__ __forceinline__ Levels levels_at(unsigned char* base, int Kmax) {
     Levels L;
@@ -736,18 +748,87 @@ enum : int { kFetch = 0, kWalk = 1, kDone = 2 };
 #define MSP_ENUM_MIN_BLOCKS(g) ((g) >= 8 ? 2 : 1)
 #endif
 
+// Fused launch: publish instance inst's subtrees (thread 0 of its block),
+// without waiting for anyone.  One atomic reserves the entry r (instances
+// counted in the high bits) and the queue positions base .. base + n - 1,
+// so the bases grow with r; the entry is written, then flagged ready.  A
+// walker holding position tk < the reserved total finds its entry by a
+// binary search over rl[0 .. r_reserved) that reads only ready entries
+// (else it keeps tk and looks again later).
+__device__ __noinline__ void publish_instance(const Pools& P, const Pipe& pipe, int inst) {
+    const InstDesc& I = P.inst[inst];
+    const unsigned long long n = (I.status == ST_OK) ? (unsigned long long)I.nprefix : 0ULL;
+    const unsigned long long old = atomicAdd(&P.ctrl->qres, (1ULL << 40) | n);
+    const int r = (int)(old >> 40);
+    const unsigned long long base = old & ((1ULL << 40) - 1ULL);
+    pipe.rl[r] = (int64_t)base;
+    pipe.rl[P.count + r] = inst;
+    P.qbase[inst] = (int64_t)base;
+    if (r + 1 == P.count) P.qbase[P.count] = (int64_t)(base + n);
+    __threadfence();
+    *(volatile int64_t*)&pipe.rl[2 * P.count + r] = 1;
+}
+
+// Fused launch: the entry of the published list whose range holds queue
+// position tk (tk < the reserved total of the r_res reserved entries), or -1
+// while an entry the search needs is not ready yet.
+__device__ __forceinline__ int find_entry(const Pools& P, const Pipe& pipe, int64_t tk, int r_res) {
+    const volatile int64_t* rl = pipe.rl;
+    int lo = 0, hi = r_res;
+    if (rl[2 * P.count] == 0) return -1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (rl[2 * P.count + mid] == 0) return -1;
+        if (rl[mid] <= tk) lo = mid; else hi = mid;
+    }
+    __threadfence();
+    return lo;
+}
+
+// Fused launch: block b prepares instances b, b + grid, ...  Warp 0 runs
+// the reduction steps (LLL, extraction and Gram-Schmidt, optional BKZ, the
+// filter tables), the whole block splits the top levels, thread 0 publishes
+// the subtrees.  The same device functions as the separate launches, so the
+// prepared instance is bit for bit the same.
+template <int G>
+__device__ __noinline__ void prepare_instances(const Pools& P, const EnumCfg& cfg, const Pipe& pipe) {
+    for (int inst = blockIdx.x; inst < P.count; inst += gridDim.x) {
+        if (threadIdx.x < 32) {
+            lll_inst(P, inst, pipe.delta, pipe.eta, pipe.lll_max_iter, pipe.max_ns);
+            extract_gso_inst(P, inst, 0);
+            if (pipe.bkz_beta >= 2) {
+                bkz_inst(P, inst, pipe.S, pipe.bkz_beta, pipe.delta, pipe.bkz_max_tours, pipe.lll_max_iter,
+                         pipe.max_ns);
+                extract_gso_inst(P, inst, 1);
+            }
+            prep_fixed_inst(P, inst, pipe.use_eps, pipe.dimPad);
+            __threadfence();
+        }
+        __syncthreads();
+        split_inst<G>(P, cfg, inst, pipe.split_depth, pipe.split_target, pipe.fcnt);
+        __syncthreads();
+        if (threadIdx.x == 0) publish_instance(P, pipe, inst);
+        __syncthreads();
+    }
+}
+
 // Variants V of the walker: 0 plain (binary bounds, depth-first), 1 binary
 // with the discrepancy bookkeeping of a limited-discrepancy iteration, 2
-// general bounds (r_max >= 1; depth-first or discrepancy search).  EXT: the
-// discrepancy bookkeeping is compiled in; BND: r_max is a run-time value and
-// leaves take the general check.  Each variant carries only the state it
-// needs, so the register budget stays with the hot loop.
+// general bounds (r_max >= 1; depth-first or discrepancy search), 3 plain in
+// the fused launch (the blocks first prepare the instances, walkers take
+// subtrees as instances are published).  EXT: the discrepancy bookkeeping is
+// compiled in; BND: r_max is a run-time value and leaves take the general
+// check; FUSED: the preparation and the published queue.  Each variant
+// carries only the state and calls it needs, so the register budget stays
+// with the hot loop.
 template <int G, int CPL, int V>
 __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
-    enum_kernel(Pools P, EnumCfg cfg, char* scratch, WalkerLayout WL) {
-    constexpr bool EXT = V != 0;
+    enum_kernel(Pools P, EnumCfg cfg, char* scratch, WalkerLayout WL, Pipe pipe) {
+    constexpr bool EXT = V == 1 || V == 2;
     constexpr bool BND = V == 2;
+    constexpr bool FUSED = V == 3;
     extern __shared__ __align__(16) unsigned char smem[];
+    if (FUSED) prepare_instances<G>(P, cfg, pipe);
     const int lg = threadIdx.x & (G - 1);
     const unsigned gmask = group_mask<G>();
     const int wib = threadIdx.x / G;
@@ -758,7 +839,8 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
     double* root_w = reinterpret_cast<double*>(ws);
     double* sigma = root_w + dimPad;
     Ctrl* ctrl = P.ctrl;
-    const int64_t total = P.qbase[P.count];
+    const int64_t total = FUSED ? 0 : P.qbase[P.count];   // (fused launch: known only at the end)
+    if (FUSED && lg == 0) L.ticket() = -1;
 
     // ---- per-walk state (uniform over the group's lanes) ----
     int state = kFetch;
@@ -797,8 +879,9 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
             int64_t gid = 0;   // this step's queue item (kept in shared memory for the walk)
             int src = 0, quit = 0;
             long long id = 0;
+            int fent = 0;      // fused launch: the published entry of the queue item
             if (lg == 0) {
-                if (!static_done) {
+                if (!static_done && !FUSED) {
                     const unsigned long long it = atomicAdd(&ctrl->qhead, 1ULL);
                     if ((int64_t)it < total) {
                         src = 1;
@@ -806,6 +889,41 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                     } else {
                         static_done = true;
                     }
+                } else if (!static_done) {
+                    // fused launch: a queue position is valid once the instance
+                    // whose range holds it is published; the walker keeps its
+                    // position until then, or until every instance is published
+                    // and the position lies past the end
+                    int64_t tk = L.ticket();
+                    if (tk < 0) tk = (int64_t)atomicAdd(&ctrl->qhead, 1ULL);
+                    const unsigned long long qr = *(volatile unsigned long long*)&ctrl->qres;
+                    const int r_res = (int)(qr >> 40);
+                    const int64_t reserved = (int64_t)(qr & ((1ULL << 40) - 1ULL));
+                    const int e = tk < reserved ? find_entry(P, pipe, tk, r_res) : -1;
+                    if (e >= 0) {
+                        src = 1;
+                        id = (long long)tk;
+                        fent = e;
+                        tk = -1;
+                    } else if (r_res >= P.count && tk >= reserved) {
+                        static_done = true;
+                        tk = -1;
+                    } else if (global_time_ns() > ctrl->deadline_ns) {
+                        // (no spin counter here: spins is per lane and must stay
+                        // equal across the group -- it gates the group's fetch)
+                        atomicExch(&ctrl->stop, 2u);
+                        quit = 1;
+                        tk = -1;
+                    } else if (*(volatile unsigned*)&ctrl->stop) {
+                        quit = 1;
+                        tk = -1;
+                    } else {
+                        // still waiting: back off, so that thousands of waiting
+                        // walkers do not hold the line of the reservation word
+                        // (and the preparing warps' memory traffic) hostage
+                        __nanosleep(4000);
+                    }
+                    L.ticket() = tk;
                 }
                 if (src == 0 && static_done) {
                     if (!idle_reg) { atomicAdd(&ctrl->idle, 1); idle_reg = 1; }
@@ -855,12 +973,17 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 if (src == 1) {
                     gid = P.qperm ? P.qperm[id] : (int64_t)id;
                     if (lg == 0) L.gid() = gid;
-                    int lo = 0, hi = P.count;
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (P.qbase[mid] <= gid) lo = mid; else hi = mid;
+                    if (FUSED) {   // the published instance whose range holds gid
+                        fent = __shfl_sync(gmask, fent, 0, G);
+                        inst = (int)((const volatile int64_t*)pipe.rl)[P.count + fent];
+                    } else {
+                        int lo = 0, hi = P.count;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (P.qbase[mid] <= gid) lo = mid; else hi = mid;
+                        }
+                        inst = lo;
                     }
-                    inst = lo;
                 } else {
                     const DonHdr* hd = reinterpret_cast<const DonHdr*>(P.don + id * P.don_stride);
                     inst = hd->inst;
@@ -877,6 +1000,21 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                             const unsigned long long k = *(volatile unsigned long long*)&P.don_seq[id] - 1;
                             atomicExch(&P.don_seq[id], k + (unsigned long long)P.don_cap);
                         }
+                        atomicSub(&ctrl->busy, 1);
+                    }
+                    src = 0;
+                }
+            }
+            if (src) {
+                // a walk starts inside its instance's levels; anything else (a
+                // descriptor or a donated slot out of range) ends as an error
+                // instead of a walk through memory it does not own
+                const InstDesc& I = P.inst[inst];
+                const int tst = (src == 1) ? I.split_level - 1
+                                           : reinterpret_cast<const DonHdr*>(P.don + id * P.don_stride)->t;
+                if (I.dd <= 0 || I.dd > Kmax || I.dim <= 0 || I.dim > dimPad || tst < 0 || tst >= I.dd) {
+                    if (lg == 0) {
+                        set_status(P.inst[inst], ST_EOVERFLOW);
                         atomicSub(&ctrl->busy, 1);
                     }
                     src = 0;
@@ -905,7 +1043,8 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                 if (src == 1) {
                     const int split_level = I.split_level;
                     t0 = split_level - 1;
-                    const int64_t fo = frontier_index(P, inst, I.front_sel, gid - P.qbase[inst]);
+                    const int64_t qb = FUSED ? *(const volatile int64_t*)&P.qbase[inst] : P.qbase[inst];
+                    const int64_t fo = frontier_index(P, inst, I.front_sel, gid - qb);
                     const int32_t* pu = P.fu + fo * P.Kmax;
                     for (int i = split_level; i < dd; ++i) {
                         const int32_t v = pu[i];
@@ -1163,7 +1302,6 @@ __global__ void __launch_bounds__(256, MSP_ENUM_MIN_BLOCKS(G))
                         }
                     }
                     if (EXT) dab += cost;
-#pragma unroll
                     {
                         // the child's W = W + xq Bq, recomputed instead of keeping the
                         // candidate vector live across the node (registers); the opaque copy
@@ -1345,22 +1483,30 @@ cudaError_t launch_start(Ctrl* ctrl, unsigned long long cap_ns, int keep, cudaSt
     return cudaGetLastError();
 }
 
-int enum_blocks_per_sm(int lanes, int threads, int dimMax, int Kmax) {
+// resident blocks per SM of the plain walker (variant 0) or of the fused
+// launch's (variant 3, which also holds the splitter's static shared memory)
+int enum_blocks_per_sm(int lanes, int threads, int dimMax, int Kmax, int variant) {
     int n = 0;
     const int cpl = pick_cpl(lanes, dimMax);
     const int smem = enum_smem_bytes(lanes, threads, Kmax);
-#define MSP_OCC(g, c)                                                                                 \
-    if (lanes == g && cpl == c) {                                                                     \
-        if (cudaFuncSetAttribute(enum_kernel<g, c, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) \
+#define MSP_OCC1(g, c, v)                                                                             \
+    {                                                                                                 \
+        if (cudaFuncSetAttribute(enum_kernel<g, c, v>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) \
                 != cudaSuccess ||                                                                     \
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<g, c, 0>, threads, smem) !=     \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, enum_kernel<g, c, v>, threads, smem) !=     \
                 cudaSuccess) {                                                                        \
             cudaGetLastError();                                                                       \
             n = 0;                                                                                    \
         }                                                                                             \
     }
+#define MSP_OCC(g, c)                                                                                 \
+    if (lanes == g && cpl == c) {                                                                     \
+        if (variant == 3) MSP_OCC1(g, c, 3)                                                           \
+        else MSP_OCC1(g, c, 0)                                                                        \
+    }
     MSP_ENUM_SHAPES(MSP_OCC)
 #undef MSP_OCC
+#undef MSP_OCC1
     return n;
 }
 
@@ -1368,8 +1514,10 @@ int64_t walker_bytes(int Kmax, int dimPad) { return WalkerLayout{Kmax, dimPad}.b
 
 int64_t donation_slot_bytes(int Kmax, int dimPad) { return donation_stride(Kmax, dimPad); }
 
+// pipe.on: the fused launch, cooperative so that every block is resident
+// (walkers wait for instances that other blocks prepare)
 cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int blocks, int threads, char* scratch,
-                        int Kmax, int dimPad, int variant, cudaStream_t st) {
+                        int Kmax, int dimPad, int variant, const Pipe& pipe, cudaStream_t st) {
     WalkerLayout W{Kmax, dimPad};
     const int cpl = pick_cpl(lanes, P.dimMax);
     const int smem = enum_smem_bytes(lanes, threads, Kmax);
@@ -1382,12 +1530,26 @@ cudaError_t launch_enum(const Pools& P, const EnumCfg& cfg, int lanes, int block
             cudaError_t e = cudaFuncSetAttribute(enum_kernel<g, c, b>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
             if (e != cudaSuccess) return e;                                                           \
         }                                                                                             \
-        enum_kernel<g, c, b><<<blocks, threads, smem, st>>>(P, cfg, scratch, W);                      \
+        if (pipe.on) {                                                                                \
+            cudaLaunchConfig_t lc = {};                                                               \
+            lc.gridDim = dim3(blocks);                                                                \
+            lc.blockDim = dim3(threads);                                                              \
+            lc.dynamicSmemBytes = smem;                                                               \
+            lc.stream = st;                                                                           \
+            cudaLaunchAttribute at[1];                                                                \
+            at[0].id = cudaLaunchAttributeCooperative;                                                \
+            at[0].val.cooperative = 1;                                                                \
+            lc.attrs = at;                                                                            \
+            lc.numAttrs = 1;                                                                          \
+            return cudaLaunchKernelEx(&lc, enum_kernel<g, c, b>, P, cfg, scratch, W, pipe);           \
+        }                                                                                             \
+        enum_kernel<g, c, b><<<blocks, threads, smem, st>>>(P, cfg, scratch, W, pipe);                \
         return cudaGetLastError();                                                                    \
     }
 #define MSP_LAUNCH(g, c)                                                                              \
     if (lanes == g && cpl == c) {                                                                     \
-        if (variant == 2) MSP_LAUNCH1(g, c, 2)                                                        \
+        if (variant == 3) MSP_LAUNCH1(g, c, 3)                                                        \
+        else if (variant == 2) MSP_LAUNCH1(g, c, 2)                                                   \
         else if (variant == 1) MSP_LAUNCH1(g, c, 1)                                                   \
         else MSP_LAUNCH1(g, c, 0)                                                                     \
     }

@@ -39,7 +39,7 @@ class msp_opts(C.Structure):
                 ("donation_capacity", C.c_int64), ("log_features", C.c_int),
                 ("lds_budget", C.c_int), ("lds_max", C.c_int), ("first_split_target", C.c_int),
                 ("bkz_beta", C.c_int), ("bkz_max_tours", C.c_int), ("replicas", C.c_int),
-                ("replica_seed", C.c_uint64), ("lds_rank", C.c_int)]
+                ("replica_seed", C.c_uint64), ("lds_rank", C.c_int), ("fuse", C.c_int)]
 
 
 class msp_stats(C.Structure):
