@@ -37,10 +37,10 @@ METRIC = "enum nodes/s; time to all sols (m=9) & first sol (m=12), learned vs pl
 # the autotuner's grid for the batch (coordinate descent, library defaults first)
 TUNE_GRID = {"lanes": (8, 16), "warps_per_block": (8, 4), "blocks_per_sm": (0, 1),
              "split_target": (0, 256, 4096, 16384)}
-DRAM_BYTES_PER_NODE = (105.400064e6 + 323.852544e6) / 268321291   # enum_kernel<8, 8, 0>, ncu
+DRAM_BYTES_PER_NODE = (126.395648e6 + 516.611072e6) / 268321291   # enum_kernel<8, 8, 0>, ncu
 # FP64 lane operations the same capture executed, per evaluated node (ncu
 # sm__sass_thread_inst_executed_op_fp64_pred_on): the counter-based FP64 work
-FP64_LANE_OPS_PER_NODE = 10288881548 / 268321291
+FP64_LANE_OPS_PER_NODE = 7249881043 / 268321291
 UNIT = "nodes/s"
 WORKLOAD = "batch of 64 fMSP instances, m~U{4..7}, n=10(m-1), D in {50,100,200}, all solutions"
 
