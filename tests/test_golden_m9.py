@@ -3,15 +3,10 @@ the GPU's complete runs are compared with: every stored x solves A x = d
 exactly (the fMSP definition of Sec. 1) for the instance regenerated from its
 seed, the planted x is among them, the sets are sorted and free of
 duplicates, and every instance of the workload is present."""
-import os
-
 import numpy as np
-import pytest
 
 from paper_2508_08702_gb300 import instances as I
 from tests.golden import m9_golden
-
-pytestmark = pytest.mark.skipif(not os.path.exists(m9_golden.PATH), reason="stored results not written yet")
 
 
 def test_stored_solutions_solve_the_instances():
