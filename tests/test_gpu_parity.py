@@ -266,3 +266,49 @@ def test_every_lane_count_on_every_width(lanes):
         assert np.array_equal(sols[i], ref.solutions), (i, inst.tag)
         assert res.stats[i]["nodes"] == ref.nodes, (i, inst.tag)
     ctx.close()
+
+
+MAXI = [I.make_instance(7100, 32, 127, 50, tag="max_m32n127"),     # the most rows, the widest lattice
+        I.make_instance(7102, 24, 127, 100, tag="max_m24n127"),
+        I.make_instance(7200, 6, 127, 100, tag="max_m6n127")]       # 58 solutions within budget 4
+
+
+@pytest.mark.parametrize("lanes", [8, 16])
+def test_maximum_sizes(lanes):
+    """n + 1 = 128 lattice coordinates and m = 32 rows, the largest the
+    library accepts: LLL and kernel bases and FP64 tables bit-exact, the
+    split prefixes exact, one discrepancy iteration of budget 4 (10^6 to
+    10^7 nodes) node- and set-exact; one row or one column more is
+    rejected with MSP_EINVAL."""
+    M = msp()
+    res, sols, ctx = run_gpu(MAXI, order=M.MSP_LDS, lds_budget=4, lanes=lanes)
+    found = 0
+    for i, inst in enumerate(MAXI):
+        red = O.lll(O.build_lattice(inst.A, inst.d))
+        assert np.array_equal(ctx.msp_export_reduced(i), red.basis), i
+        kern = O.extract(red.basis, inst.m)
+        g = O.gso(kern)
+        kb, mu, B, bhat = ctx.msp_export_gso(i)
+        assert kb.shape[1] == 128
+        assert np.array_equal(kb, kern), i
+        assert np.array_equal(B, g.B), i
+        assert np.array_equal(np.tril(mu), np.tril(g.mu)), i
+        assert np.array_equal(bhat, g.bhat), i
+        ref = O.enumerate(kern, g, inst.A, inst.d, lanes=lanes, lds=4)
+        st = res.stats[i]
+        assert (st["nodes"], st["passed"], st["leaves"]) == (ref.nodes, ref.passed, ref.leaves), (i, lanes)
+        assert np.array_equal(sols[i], ref.solutions), i
+        found += len(ref.solutions)
+        p = ctx.msp_export_prefixes(i)
+        lvl = p["split_level"]
+        top = O.enumerate(kern, g, inst.A, inst.d, lanes=lanes, split_level=lvl, lds=4)   # budgeted top levels
+        assert np.array_equal(p["u"][:, lvl:], top.prefixes[:, lvl:]), i
+        assert np.array_equal(p["rho"], top.prefix_rho), i
+    assert found > 0
+    ctx.close()
+    ctx = M.Context()
+    for m, n in [(1, 128), (33, 40)]:
+        with pytest.raises(M.MspError) as e:
+            ctx.msp_build_lattice(np.array([[m, n]]), np.zeros(m * n, np.int32), np.zeros(m, np.int64))
+        assert e.value.status == M.MSP_EINVAL, (m, n)
+    ctx.close()
