@@ -1435,15 +1435,15 @@ __global__ void sol_rank_kernel(Pools P, const int64_t* soff, const SolRec* seg,
 // Host-side launch helpers (called from api.cu).
 // ---------------------------------------------------------------------------
 // (G, CPL) instances: CPL = coordinates per lane, G * CPL >= n + 1
-#define MSP_ENUM_SHAPES(X) X(4, 16) X(4, 32) X(8, 8) X(8, 16) X(16, 4) X(16, 8) X(32, 4)
+#define MSP_ENUM_SHAPES(X) X(4, 16) X(4, 32) X(8, 8) X(8, 16) X(16, 4) X(16, 6) X(16, 8) X(32, 4)
 
 static int pick_cpl(int lanes, int dimMax) {
     const int need = (dimMax + lanes - 1) / lanes;
-    const int opts[] = {4, 8, 16, 32};
+    const int opts[] = {4, 6, 8, 16, 32};
     for (int c : opts) {
         if (c < need) continue;
         switch (lanes * 100 + c) {
-            case 416: case 432: case 808: case 816: case 1604: case 1608: case 3204: return c;
+            case 416: case 432: case 808: case 816: case 1604: case 1606: case 1608: case 3204: return c;
             default: break;
         }
     }
