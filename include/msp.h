@@ -60,11 +60,12 @@ typedef enum { MSP_ALL = 0, MSP_FIRST = 1 } msp_mode;      /* all solutions / st
  * in depth-first order.  LEARNED: the subtrees ranked by the scorer
  * (msp_set_scorer); the walk inside a subtree stays depth-first.  LDS:
  * limited discrepancy search (Sec. 3): iterations k = 0, 1, 2, ... each walk
- * Algorithm 1 trying a value other than the first of its level (the rounded
- * centre) only while the path above carries fewer than k such
- * discrepancies, and report the leaves with exactly k; MSP_FIRST stops an
- * instance at its first solution, MSP_ALL when an iteration held no value
- * back (every solution is then reported exactly once).  LDS_LEARNED: limited
+ * Algorithm 1 but try a value only while the discrepancy cost of the path
+ * (the sum over its levels of the value's cost, opts.lds_rank; the first
+ * value of a level, the rounded centre, costs 0) stays at most k, and report
+ * the leaves whose path costs exactly k; MSP_FIRST stops an instance at its
+ * first solution, MSP_ALL when an iteration held no value back (every
+ * solution is then reported exactly once).  LDS_LEARNED: limited
  * discrepancy search whose iterations take their subtrees in the scorer's
  * order (as LEARNED does; the same nodes and solutions as LDS, possibly
  * sooner). */
@@ -91,7 +92,7 @@ typedef struct {
     int split_target;      /* [0] stop splitting once an instance has this many subtree   */
                            /*     prefixes (0: 8 x the number of walkers / instances)     */
     int split_capacity;    /* [0] prefixes stored per instance (0: 4 x split_target)      */
-    int warps_per_block;   /* [8] enumerator block size in warps                          */
+    int warps_per_block;   /* [8] enumerator block size in warps, 1 to 8                  */
     int blocks_per_sm;     /* [0] enumerator blocks per SM (0: as many as can be resident; */
                            /*     larger values are capped at that)                     */
     int64_t sol_capacity;  /* [1<<20] solutions stored (over all instances)               */
@@ -224,8 +225,11 @@ MSP_API msp_status msp_reduce(msp_ctx *ctx);
 /* Steps a4-a7 -- Algorithm 1: split the top levels into subtree prefixes,
  * optionally reorder them by the learned scorer (MSP_LEARNED; falls back
  * to MSP_PLAIN when no scorer is loaded), enumerate every subtree on the
- * device and check every leaf exactly (Theorem 1).  MSP_FIRST stops all
- * walkers once one solution is verified.  time_cap_s > 0 bounds the
+ * device and check every leaf exactly (Theorem 1).  MSP_FIRST finishes
+ * each instance (with its replicas) at its first verified solution: its
+ * remaining subtrees are skipped while the other instances of the batch go
+ * on, and the launch ends once every instance is solved or its tree is
+ * exhausted.  time_cap_s > 0 bounds the
  * enumeration's wall time (MSP_ETIMEOUT, partial results).
  * stats: NULL or count entries (one per instance).  total: NULL or one
  * entry summed over the batch.  Synchronises the stream. */
