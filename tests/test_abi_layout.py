@@ -6,7 +6,8 @@ every later field without any error.  These tests compile a small C program
 against include/msp.h with the host compiler and compare the field names,
 order, offsets and sizes with the ctypes structures, and check that every
 default the header documents in brackets is what msp_default_opts() writes.
-No device is needed.
+The argument and return types the binding declares for every function are
+compared with the header's prototypes the same way.  No device is needed.
 """
 import ctypes
 import os
@@ -108,3 +109,53 @@ def test_documented_defaults_are_the_library_defaults():
     assert all(d is not None for _, d in documented), [f for f, d in documented if d is None]
     for f, d in documented:
         assert getattr(o, f) == _value(d), (f, d, getattr(o, f))
+
+
+SCALARS = {"int": ctypes.c_int, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+           "double": ctypes.c_double, "float": ctypes.c_float, "size_t": ctypes.c_size_t}
+
+
+def header_prototypes():
+    """{name: (return type text, [parameter type texts])} of the MSP_API functions."""
+    src = re.sub(r"/\*.*?\*/", " ", open(HEADER).read(), flags=re.S)
+    out = {}
+    for ret, name, params in re.findall(r"MSP_API\s+([\w\s\*]+?)\s*\b(msp_\w+)\s*\(([^)]*)\)\s*;", src):
+        ps = [" ".join(p.split()) for p in params.split(",")]
+        ps = [] if ps == ["void"] else ps
+        # drop the parameter name, keep the type
+        types = [re.sub(r"\s*\b\w+$", "", p) if not p.endswith("*") else p for p in ps]
+        out[name] = (" ".join(ret.split()), types)
+    return out
+
+
+def _matches(ctext, ct):
+    """Whether ctypes type ct passes a C parameter or return value of type ctext."""
+    t = ctext.replace("const ", "").strip()
+    if t.endswith("*"):
+        if t == "char *":
+            return ct is ctypes.c_char_p
+        return ct is ctypes.c_void_p or (isinstance(ct, type) and issubclass(ct, ctypes._Pointer))
+    if t in ("msp_status", "int"):
+        return ct is ctypes.c_int
+    return ct is SCALARS[t]
+
+
+def test_binding_signatures_follow_the_header():
+    from paper_2508_08702_gb300 import build
+    try:
+        build.build()
+    except (RuntimeError, FileNotFoundError) as e:   # no nvcc on this machine
+        pytest.skip(f"cannot build the CUDA library here: {e}")
+    L = msp().load()
+    protos = header_prototypes()
+    assert len(protos) == len(re.findall(r"^MSP_API", open(HEADER).read(), re.M))
+    for name, (ret, params) in protos.items():
+        fn = getattr(L, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == len(params), (name, params)
+        for ctext, ct in zip(params, fn.argtypes):
+            assert _matches(ctext, ct), (name, ctext, ct)
+        if ret == "void":
+            assert fn.restype is None, name
+        else:
+            assert _matches(ret, fn.restype), (name, ret, fn.restype)
