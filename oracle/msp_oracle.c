@@ -10,8 +10,10 @@
  *   1. lattice build        generator matrix of Eq. (2), binary case
  *                           r_max = c_j = 1                     [Sec. 2]
  *   2. LLL                  integral basis, exact int64 Gram matrix,
- *                           FP64 Gram-Schmidt recomputed per row
- *                           (Schnorr-Euchner style lazy size reduction)
+ *                           FP64 Gram-Schmidt recomputed per row from the
+ *                           Gram matrix, one size-reduction pass per row
+ *                           (repeated until nothing changes in the LLL
+ *                           inside BKZ; reading R10)
  *                                                    [Sec. 2, Alg. 1 step 1]
  *   3. extraction           keep the vectors whose first m entries are zero,
  *                           drop those m rows          [Sec. 2, Alg. 1 step 2]
