@@ -65,8 +65,10 @@
  *       reduction of a row: one pass j = k-1 .. 0 on its freshly computed
  *       Gram-Schmidt row, updated in place; the LLL inside BKZ repeats the
  *       pass until nothing changes (see oracle_lll).
- *   R11 Instances are made feasible by a planted binary x, d = A x (the
- *       construction of the paper's instance library is not described).
+ *   R11 The construction of the paper's instance library is not described.
+ *       The configurations plant a binary x and set d = A x; the stand-ins
+ *       for the rows of the paper's timing table use the centred right-hand
+ *       side d_i = floor(sum_j a_ij / 2).  The oracle takes A and d as given.
  *   R12 Limited discrepancy search (Sec. 3, after Harvey and Ginsberg): a
  *       discrepancy is a deviation from the heuristic order of a level's
  *       walk, whose first value u^1 is the rounded centre (0 on the all-zero
