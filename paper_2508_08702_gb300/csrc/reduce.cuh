@@ -12,11 +12,15 @@
 // step and over the instances of a batch.  Every floating-point operation
 // is an explicit IEEE intrinsic (no contraction), in the fixed order:
 //   r_kj = G_kj - sum_{i<j} mu_ji r_ki  (ascending i, one fma per term),
-//   mu_kj = r_kj / r_jj,  B_k = r_kk  (same fold with mu_ki),
-// size reduction of b_k against b_j for j = k-1 .. 0 while |mu_kj| > eta,
-// with q = rint(mu_kj), mu_ki <- fma(-q, mu_ji, mu_ki) (i < j), mu_kj <- mu_kj - q,
-// then the Gram row of b_k recomputed exactly and the row redone; Lovasz:
-// swap iff B_k < (delta - mu_{k,k-1}^2) B_{k-1}, each operation rounded.
+//   B_k = r_kk  (same fold with mu_ki); inside the reduction
+//   mu_kj = r_kj * (1 / r_jj) with the reciprocal formed once per row, in
+//   the enumeration tables mu_kj = r_kj / r_jj (Eq. (4) as written),
+// size reduction of b_k against b_j in one pass j = k-1 .. 0 where
+// |mu_kj| > eta, with q = rint(mu_kj), mu_ki <- fma(-q, mu_ji, mu_ki) (i < j),
+// mu_kj <- mu_kj - q, then the Gram row of b_k recomputed exactly (the LLL
+// inside BKZ redoes the row and repeats the pass until nothing changes);
+// Lovasz: swap iff B_k < (delta - mu_{k,k-1}^2) B_{k-1}, each operation
+// rounded.
 #pragma once
 #include "common.cuh"
 
