@@ -1,0 +1,187 @@
+"""Planted mistakes in the oracle are caught by its pins.
+
+The oracle is trusted because tests pin it to things it does not compute
+itself (brute force, exact rationals, the lattice of Eq. (2)).  This file
+checks that those pins are strong enough: each mutant below is a copy of
+oracle/msp_oracle.c with one plausible mistake -- a dropped term, a wrong
+sign or index, a misread reading -- compiled to a temporary library.  A
+child process runs a fast selection of the pins against it, and every
+mutant must fail at least one of them, while the unmodified source passes
+all of them.  Nothing here touches the product path or a GPU.
+"""
+import json
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "msp_oracle.c")
+
+# (name, function the change is made in, text, replacement): the first
+# occurrence of the text after the start of that function is replaced.
+# Every mutant ends within seconds (a partial norm that drops rho_{t+1}
+# instead of doubling it would also be wrong, but its tree never stops
+# growing, so it is not used here).
+MUTANTS = [
+    ("centre from the transposed mu entry", "static double center(",
+     "e->mu[(size_t)i * e->dd + t]", "e->mu[(size_t)t * e->dd + i]"),
+    ("centre of the wrong sign", "static void enum_level(",
+     "const double cstar = -y;", "const double cstar = y;"),
+    ("partial norm with rho_{t+1} counted twice", "static void enum_level(",
+     "fma(xx, e->B[t], rho_p)", "fma(xx, e->B[t], 2.0 * rho_p)"),
+    ("w updated from the wrong row of bhat", "static void enum_level(",
+     "e->bhat[(size_t)t * dim + c]", "e->bhat[(size_t)(t - 1) * dim + c]"),
+    ("l1 norm without the absolute value", "static double norm1(",
+     "fabs(w[c])", "w[c]"),
+    ("zig-zag starting on the wrong side", "static void enum_level(",
+     "int s = (cstar >= (double)u1) ? 1 : -1;", "int s = (cstar >= (double)u1) ? -1 : 1;"),
+    ("one-direction phase walking back past the centre", "static void enum_level(",
+     "dir = (u > u1) ? 1 : -1;", "dir = (u > u1) ? -1 : 1;"),
+    ("next() skipping every other value", "static void enum_level(",
+     "else { zi += 1; u = zigzag(u1, s, zi); }", "else { zi += 2; u = zigzag(u1, s, zi); }"),
+    ("leaf without sign normalisation", "static int leaf_check(",
+     "if (last == -rmax)", "if (0 && last == -rmax)"),
+    ("no slack on the bounds", "int oracle_enumerate_bounds(",
+     "e.eps = o->use_eps ? R * 0x1p-20 : 0.0;", "e.eps = 0.0;"),
+    ("Lovasz test with a smaller delta", "static int lll_core(",
+     "if (B[k] < rhs)", "if (B[k] < 0.5 * rhs)"),
+    ("size reduction updating mu with the wrong sign", "static int lll_core(",
+     "fma(-qd, mu", "fma(qd, mu"),
+    ("Gram-Schmidt mu divided by the first B", "int oracle_gso(",
+     "mu[(size_t)i * dd + j] = acc / B[j];", "mu[(size_t)i * dd + j] = acc / B[0];"),
+    ("lattice with +N d in the first column", "int oracle_build_lattice_bounds(",
+     "i128 v = -(i128)N * (i128)d[i];", "i128 v = (i128)N * (i128)d[i];"),
+]
+
+
+def mutate(src, where, old, new):
+    start = src.index(where)
+    at = src.index(old, start)
+    return src[:at] + new + src[at + len(old):]
+
+
+def compile_library(source_text, out_dir, tag):
+    """The oracle's own build flags (oracle/build.py) on a copy of the source."""
+    c = os.path.join(out_dir, f"{tag}.c")
+    so = os.path.join(out_dir, f"{tag}.so")
+    with open(c, "w") as f:
+        f.write(source_text)
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                    "-o", so, c, "-lm"], check=True, capture_output=True)
+    return so
+
+
+# --------------------------------------------------------------------------
+# child process: the pins, run against the library at sys.argv[1]
+
+def _pins():
+    import numpy as np
+
+    from oracle import definition as DEF
+    from oracle import oracle as O
+    import test_oracle_counts as TC
+    import test_oracle_enum as TE
+    import test_oracle_lattice as TL
+
+    def sets():
+        """solution sets equal brute force (1 and 8 lanes; all pruning modes)"""
+        for k, inst in enumerate(TE.SMALL[:12]):
+            want = DEF.brute_force(inst.A, inst.d)
+            for lanes in (1, 8):
+                got = O.solve(inst.A, inst.d, lanes=lanes).result.solutions
+                assert np.array_equal(got, want), (k, lanes)
+            for hoelder, sym in TE.MODES[1:]:
+                got = O.solve(inst.A, inst.d, hoelder=hoelder, sym=sym).result.solutions
+                assert np.array_equal(got, want), (k, hoelder, sym)
+
+    def lattice():
+        for c in TL.CASES:
+            TL.test_lattice_contains_planted_solution(c)
+
+    def lll():
+        for c in TL.CASES:
+            TL.test_lll_is_unimodular_and_reduced(c)
+
+    def gso():
+        for c in TL.CASES:
+            TL.test_gso_against_exact_rationals(c)
+
+    def counts():
+        for inst in TC.CASES[:3]:
+            for sym in (False, True):
+                for mode in (O.HOELDER_OFF, O.HOELDER_FILTER):
+                    TC.test_counts_equal_the_definition(inst, sym, mode)
+
+    return {"sets": sets, "lattice": lattice, "lll": lll, "gso": gso, "counts": counts}
+
+
+def child_main(lib_path):
+    from oracle import build as OB
+    from oracle import oracle as O
+    OB.build = lambda force=False: lib_path
+    O._lib = None
+    out = {}
+    for name, fn in _pins().items():
+        try:
+            fn()
+            out[name] = "pass"
+        except (KeyboardInterrupt, SystemExit):
+            raise
+        except BaseException as e:   # assertion, oracle error, pytest outcome
+            out[name] = f"fail: {type(e).__name__}: {str(e)[:160]}"
+    print(json.dumps(out), flush=True)
+
+
+CHILD = ("import sys; sys.path[:0] = [{root!r}, {tests!r}]; "
+         "import test_oracle_mutations as t; t.child_main(sys.argv[1])").format(
+    root=ROOT, tests=os.path.join(ROOT, "tests"))
+
+
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    import shutil
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    out_dir = str(tmp_path_factory.mktemp("mutants"))
+    src = open(SRC).read()
+    jobs = [("unmodified", src)] + [(name, mutate(src, where, old, new)) for name, where, old, new in MUTANTS]
+
+    def run(job):
+        i, (name, text) = job
+        so = compile_library(text, out_dir, f"oracle{i}")
+        try:
+            r = subprocess.run([sys.executable, "-c", CHILD, so], capture_output=True, text=True, timeout=300,
+                               cwd=ROOT)
+        except subprocess.TimeoutExpired:
+            return name, {"run": "fail: timed out"}
+        if r.returncode != 0:
+            return name, {"run": f"fail: exit {r.returncode}: {r.stderr[-200:]}"}
+        return name, json.loads(r.stdout.strip().splitlines()[-1])
+
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        return dict(ex.map(run, enumerate(jobs)))
+
+
+def test_mutations_apply_once_inside_their_function():
+    src = open(SRC).read()
+    for name, where, old, new in MUTANTS:
+        assert src.count(where) == 1, name
+        start = src.index(where)
+        nxt = src.find("\n}\n", start)      # end of that function
+        assert start < src.index(old, start) < nxt, name
+
+
+def test_the_unmodified_oracle_passes_every_pin(outcomes):
+    res = outcomes["unmodified"]
+    assert res and all(v == "pass" for v in res.values()), res
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_each_planted_mistake_fails_a_pin(outcomes, name):
+    res = outcomes[name]
+    assert any(v != "pass" for v in res.values()), res
