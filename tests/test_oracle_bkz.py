@@ -10,6 +10,8 @@ Checked against things the C code does not compute itself:
     delta of the block's shortest nonzero projected vector, found here by an
     independent exact-rational search on small lattices;
   * with beta = dd the first vector is a shortest vector of the lattice;
+  * on instances whose LLL basis is not block-reduced and does not start
+    with a shortest vector, BKZ inserts vectors and repairs both;
   * enumeration on the BKZ basis finds the brute-force solution set.
 """
 from fractions import Fraction
@@ -127,6 +129,41 @@ def test_full_block_gives_a_shortest_vector():
     mu, B = exact_gso(kb)
     lam = block_shortest(mu, B, 0, dd)
     assert float(B[0]) <= float(lam) / 0.999999 * (1 + 1e-12)
+
+
+# Instances on which LLL leaves work for the block search: some block of
+# width 4 of the LLL basis is not delta-reduced, and its first vector is not
+# a shortest one (squared norms 24 against 20, and 73 against 25).  On the
+# small-D cases above the LLL basis often passes these checks already, so
+# only these show that the block search finds and inserts what is missing.
+HARD = [I.small(2003, 2, 20, 200), I.small(2005, 3, 24, 1000)]
+
+
+@pytest.mark.parametrize("inst", HARD, ids=lambda x: x.tag)
+def test_block_search_repairs_what_lll_leaves(inst):
+    beta, delta = 4, Fraction(99, 100)
+    _, kern, _ = O.reduce(inst.A, inst.d)
+    mu0, B0 = exact_gso(kern)
+    dd = len(B0)
+    assert any(delta * B0[k] > block_shortest(mu0, B0, k, min(k + beta, dd)) for k in range(dd - 1))
+    r = O.bkz(kern, beta, delta=0.99)
+    assert r.inserts > 0
+    mu, B = exact_gso(r.kern)
+    for k in range(dd - 1):
+        lam = block_shortest(mu, B, k, min(k + beta, dd))
+        assert float(delta * B[k]) <= float(lam) * (1 + 1e-12), k
+
+
+@pytest.mark.parametrize("inst", HARD, ids=lambda x: x.tag)
+def test_full_block_finds_the_shortest_vector_lll_missed(inst):
+    _, kern, _ = O.reduce(inst.A, inst.d)
+    mu0, B0 = exact_gso(kern)
+    dd = len(B0)
+    lam = block_shortest(mu0, B0, 0, dd)
+    assert B0[0] > lam
+    kb = O.bkz(kern, dd, delta=0.999999).kern
+    # ||b_0||^2 is an integer and at most lam / 0.999999, so it equals lam
+    assert int(np.dot(kb[0].astype(np.int64), kb[0].astype(np.int64))) == lam
 
 
 @pytest.mark.parametrize("inst", CASES, ids=lambda x: x.tag)
