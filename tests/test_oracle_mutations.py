@@ -54,6 +54,14 @@ MUTANTS = [
      "mu[(size_t)i * dd + j] = acc / B[j];", "mu[(size_t)i * dd + j] = acc / B[0];"),
     ("lattice with +N d in the first column", "int oracle_build_lattice_bounds(",
      "i128 v = -(i128)N * (i128)d[i];", "i128 v = (i128)N * (i128)d[i];"),
+    ("rank discrepancy counted from one", "static int value_cost(",
+     "e->o.lds_rank ? (int)pos", "e->o.lds_rank ? (int)pos + 1"),
+    ("flat discrepancy counting only values above the first", "static int value_cost(",
+     "(u != u1)", "(u > u1)"),
+    ("block search centred with the wrong sign", "static void svp_level(",
+     "cstar = -y;", "cstar = y;"),
+    ("bounded leaf without the per-variable scale c_j", "static int leaf_check(",
+     "const int64_t cc = 2 * (rmax / (e->r ? e->r[c] : 1));", "const int64_t cc = 2 * rmax;"),
 ]
 
 
@@ -115,10 +123,35 @@ def _pins():
                 for mode in (O.HOELDER_OFF, O.HOELDER_FILTER):
                     TC.test_counts_equal_the_definition(inst, sym, mode)
 
-    return {"sets": sets, "lattice": lattice, "lll": lll, "gso": gso, "counts": counts}
+    def lds():
+        import test_oracle_lds as TD
+        for rank in (False, True):
+            for inst in TD.CASES[:3]:
+                TD.test_iterations_partition_the_solution_set(inst, rank)
+            TD.test_first_solution_comes_at_the_least_discrepancy(rank)
+
+    def bkz():
+        import test_oracle_bkz as TB
+        TB.test_same_lattice_and_volume(TB.CASES[0], 4)
+        for inst in TB.CASES[:2]:
+            TB.test_blocks_are_reduced(inst)
+        TB.test_full_block_gives_a_shortest_vector()
+        for inst in TB.HARD:
+            TB.test_block_search_repairs_what_lll_leaves(inst)
+            TB.test_full_block_finds_the_shortest_vector_lll_missed(inst)
+
+    def bounds():
+        import test_oracle_bounds as TN
+        for inst in TN.CASES[:3]:
+            TN.test_bounded_solution_sets_equal_brute_force(inst, O.HOELDER_CUT, True)
+
+    return {"sets": sets, "lattice": lattice, "lll": lll, "gso": gso, "counts": counts, "lds": lds, "bkz": bkz,
+            "bounds": bounds}
 
 
-def child_main(lib_path):
+def child_main(lib_path, stop_at_first=True):
+    """Runs the pins in order; a mutant stops at its first failure (a wrong
+    table can make a later, larger search run very long)."""
     from oracle import build as OB
     from oracle import oracle as O
     OB.build = lambda force=False: lib_path
@@ -132,6 +165,8 @@ def child_main(lib_path):
             raise
         except BaseException as e:   # assertion, oracle error, pytest outcome
             out[name] = f"fail: {type(e).__name__}: {str(e)[:160]}"
+            if stop_at_first:
+                break
     print(json.dumps(out), flush=True)
 
 
