@@ -165,3 +165,62 @@ def test_filter_prunes_and_the_cut_prunes_more():
     cut = O.enumerate(kern, g, inst.A, inst.d, hoelder=O.HOELDER_CUT)
     assert cut.nodes <= filt["nodes"]
     assert np.array_equal(cut.solutions, O.enumerate(kern, g, inst.A, inst.d, hoelder=O.HOELDER_OFF).solutions)
+
+
+def exact_prefixes(kern, split_level, sym):
+    """Every prefix (u_split_level, ..., u_{d-1}) whose partial norms stay
+    within R + eps at each of its levels, with rho at the split level, in
+    exact rationals (the split of the tree at `split_level` with the Hoelder
+    test off)."""
+    mu, B, _ = exact_gso(kern)
+    dd = len(B)
+    Rb = Fraction(kern.shape[1]) * (1 + Fraction(1, 2 ** 20))
+    u = [0] * dd
+    out = {}
+
+    def rec(t, rho, zero):
+        c = -sum(u[i] * mu[i][t] for i in range(t + 1, dd))
+        span = (Rb - rho) / B[t]
+        if span < 0:
+            return
+        r = math.isqrt(span.numerator // span.denominator) + 1
+        lo, hi = math.floor(c) - r - 1, math.ceil(c) + r + 1
+        if zero and sym:
+            lo = max(lo, 0)
+        for x in range(lo, hi + 1):
+            d = rho + (x - c) ** 2 * B[t]
+            if d > Rb:
+                continue
+            u[t] = x
+            if t == split_level:
+                out[tuple(u[split_level:])] = d
+            else:
+                rec(t - 1, d, zero and x == 0)
+        u[t] = 0
+
+    rec(dd - 1, Fraction(0), True)
+    return out
+
+
+@pytest.mark.parametrize("inst", CASES[:4], ids=lambda x: x.tag)
+@pytest.mark.parametrize("sym", [False, True], ids=["literal", "sym"])
+def test_split_prefixes_and_their_norms_are_exact(inst, sym):
+    """The split the GPU splitter is compared with: with the Hoelder test
+    off the recorded prefixes are exactly the paths inside the norm bound,
+    and each recorded rho is the exact partial norm of its prefix; with the
+    default one-direction cut every recorded prefix is one of those paths,
+    with the same exact rho."""
+    _, kern, g = O.reduce(inst.A, inst.d)
+    dd = kern.shape[0]
+    for split_level in (dd - 3, dd - 6):
+        want = exact_prefixes(kern, split_level, sym)
+        for hoelder in (O.HOELDER_OFF, O.HOELDER_CUT):
+            top = O.enumerate(kern, g, inst.A, inst.d, hoelder=hoelder, sym=sym, split_level=split_level)
+            got = {tuple(int(v) for v in p[split_level:]): float(r) for p, r in zip(top.prefixes, top.prefix_rho)}
+            assert len(got) == top.nprefix
+            if hoelder == O.HOELDER_OFF:
+                assert set(got) == set(want)
+            else:
+                assert set(got) <= set(want)
+            for key, rho in got.items():
+                assert rho == pytest.approx(float(want[key]), rel=1e-12, abs=1e-12), key

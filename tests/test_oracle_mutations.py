@@ -60,6 +60,8 @@ MUTANTS = [
      "(u != u1)", "(u > u1)"),
     ("block search centred with the wrong sign", "static void svp_level(",
      "cstar = -y;", "cstar = y;"),
+    ("split prefix recorded with the parent's partial norm", "static void enum_level(",
+     "e->pre_rho[p] = rho;", "e->pre_rho[p] = rho_p;"),
     ("bounded leaf without the per-variable scale c_j", "static int leaf_check(",
      "const int64_t cc = 2 * (rmax / (e->r ? e->r[c] : 1));", "const int64_t cc = 2 * rmax;"),
 ]
@@ -123,6 +125,11 @@ def _pins():
                 for mode in (O.HOELDER_OFF, O.HOELDER_FILTER):
                     TC.test_counts_equal_the_definition(inst, sym, mode)
 
+    def split():
+        for inst in TC.CASES[:2]:
+            for sym in (False, True):
+                TC.test_split_prefixes_and_their_norms_are_exact(inst, sym)
+
     def lds():
         import test_oracle_lds as TD
         for rank in (False, True):
@@ -145,7 +152,7 @@ def _pins():
         for inst in TN.CASES[:3]:
             TN.test_bounded_solution_sets_equal_brute_force(inst, O.HOELDER_CUT, True)
 
-    return {"sets": sets, "lattice": lattice, "lll": lll, "gso": gso, "counts": counts, "lds": lds, "bkz": bkz,
+    return {"sets": sets, "lattice": lattice, "lll": lll, "gso": gso, "counts": counts, "split": split, "lds": lds, "bkz": bkz,
             "bounds": bounds}
 
 
