@@ -62,6 +62,17 @@ MUTANTS = [
      "cstar = -y;", "cstar = y;"),
     ("split prefix recorded with the parent's partial norm", "static void enum_level(",
      "e->pre_rho[p] = rho;", "e->pre_rho[p] = rho_p;"),
+    ("extraction testing one row too few", "int oracle_extract(",
+     "for (int i = 0; i < m; ++i) if (b[i] != 0)", "for (int i = 0; i < m - 1; ++i) if (b[i] != 0)"),
+    ("bounded lattice without c_j on the diagonal", "int oracle_build_lattice_bounds(",
+     "b[m + (j - 1)] = 2 * (rmax / (r ? r[j - 1] : 1));", "b[m + (j - 1)] = 2;"),
+    ("l1 lane tree missing its last combine", "static double norm1(",
+     "for (int off = G / 2; off >= 1; off /= 2)", "for (int off = G / 2; off > 1; off /= 2)"),
+    ("discrepancy leaves reported below the budget", "static void enum_level(",
+     "disc + cost == e->o.lds", "disc + cost <= e->o.lds"),
+    ("leaf without the range check on v", "static int leaf_check(",
+     "if (v[c] > rmax || v[c] < -rmax || (v[c] + rmax) % cc != 0) return 0;",
+     "if ((v[c] + rmax) % cc != 0) return 0;"),
     ("bounded leaf without the per-variable scale c_j", "static int leaf_check(",
      "const int64_t cc = 2 * (rmax / (e->r ? e->r[c] : 1));", "const int64_t cc = 2 * rmax;"),
 ]
@@ -110,6 +121,7 @@ def _pins():
     def lattice():
         for c in TL.CASES:
             TL.test_lattice_contains_planted_solution(c)
+            TL.test_extraction_is_a_kernel_basis(c)
 
     def lll():
         for c in TL.CASES:
@@ -149,6 +161,7 @@ def _pins():
 
     def bounds():
         import test_oracle_bounds as TN
+        TN.test_lattice_columns()
         for inst in TN.CASES[:3]:
             TN.test_bounded_solution_sets_equal_brute_force(inst, O.HOELDER_CUT, True)
 
