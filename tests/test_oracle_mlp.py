@@ -2,8 +2,8 @@
 
 The loss gradient is checked against central finite differences of the
 loss on the exact (unrounded) network -- a wrong sign, a dropped term or a
-transposed weight in the backward formulas fails here -- and the bfloat16
-rounding against values worked out by hand."""
+transposed weight in the backward formulas fails here -- and the forward
+pass and the bfloat16 rounding against values worked out by hand."""
 import numpy as np
 import pytest
 
@@ -45,6 +45,40 @@ def test_gradient_matches_finite_differences(pos_weight):
         fm, _ = R.loss_and_grad(tm, x, found, ln, pos_weight, round_bf16=False)
         num = (fp - fm) / (2 * h)
         assert num == pytest.approx(g[i], rel=1e-5, abs=1e-8), i
+
+
+@pytest.mark.parametrize("round_bf16", [False, True])
+def test_forward_by_hand(round_bf16):
+    """A network with a handful of nonzero weights, every value exact in
+    bfloat16, worked out by hand (32 -> 64 -> 64 -> 8, ReLU, row = input):
+      layer 1: a = (2 * 1.5 + 0.5, -1 * 3 + 0.25) = (3.5, -2.75) -> h1 = (3.5, 0)
+      layer 2: a = (1 * 3.5, -2 * 3.5 + 1, 0.75, -1 * 0) = (3.5, -6, 0.75, 0)
+               -> h2 = (3.5, 0, 0.75, 0)
+      layer 3: y0 = 2 * 3.5 - 1 = 6, y1 = 4 * 0.75 + 0.5 = 3.5, y2 = 8 * 0 = 0,
+               y3 = 1 * 0 = 0, y7 = b3[7] = -0.125
+    A missing ReLU (y2 = -48 or y3 = 2.75), a transposed layer or a dropped
+    bias changes y."""
+    p = R.unpack(np.zeros(R.MLP_PARAMS))
+    p["W1"][0, 0], p["W1"][1, 1] = 2.0, -1.0
+    p["b1"][0], p["b1"][1] = 0.5, 0.25
+    p["W2"][0, 0], p["W2"][0, 1], p["W2"][1, 3] = 1.0, -2.0, -1.0
+    p["b2"][1], p["b2"][2] = 1.0, 0.75
+    p["W3"][0, 0], p["W3"][2, 1], p["W3"][1, 2], p["W3"][3, 3] = 2.0, 4.0, 8.0, 1.0
+    p["b3"][0], p["b3"][1], p["b3"][7] = -1.0, 0.5, -0.125
+    x = np.zeros((2, 32))
+    x[0, 0], x[0, 1] = 1.5, 3.0
+    y, _ = R.forward(R.pack(p), x, round_bf16=round_bf16)
+    want = np.zeros((2, 8))
+    want[0, :3] = [6.0, 3.5, 0.0]
+    want[:, 7] = -0.125
+    # the second row's input is zero: h1 = relu(b1) = (0.5, 0.25),
+    # h2 = relu(0.5, -2 * 0.5 + 1, 0.75, -0.25) = (0.5, 0, 0.75, 0)
+    h1 = np.array([0.5, 0.25])
+    h2 = np.array([h1[0], -2 * h1[0] + 1.0, 0.75])
+    want[1, 0] = 2 * h2[0] - 1.0
+    want[1, 1] = 4 * h2[2] + 0.5
+    want[1, 2] = 8 * max(h2[1], 0.0)
+    assert np.array_equal(y, want)
 
 
 def test_score_ranks_by_solution_probability():
