@@ -13,6 +13,24 @@ def test_splitmix64_reference_output():
     assert next(RP.splitmix64(0)) == 0xE220A8397B1DCDAF
 
 
+def test_splitmix64_reference_sequence():
+    """The first four outputs from state 0 of the published reference
+    implementation."""
+    g = RP.splitmix64(0)
+    assert [next(g) for _ in range(4)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                           0x06C45D188009454F, 0xF88BB8A8724C81EC]
+
+
+def test_fisher_yates_by_hand():
+    """Replica 1 of instance 0 with seed 1 starts the stream at state
+    1 ^ (0 << 32) ^ 1 = 0, so its z are the outputs above.  n = 4, from the
+    identity (0, 1, 2, 3):
+      j = 3: z1 mod 4 = 3 (last hex digit F = 15)        -> swap 3, 3: (0, 1, 2, 3)
+      j = 2: z2 mod 3 = 0 (hex digit sum 135, 16 = 1 mod 3) -> swap 2, 0: (2, 1, 0, 3)
+      j = 1: z3 mod 2 = 1 (last hex digit F, odd)          -> swap 1, 1: (2, 1, 0, 3)"""
+    assert RP.permutation(4, 0, 1, seed=1).tolist() == [2, 1, 0, 3]
+
+
 def test_permutations_are_permutations_and_differ():
     seen = set()
     for k in range(1, 6):
