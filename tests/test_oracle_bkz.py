@@ -94,18 +94,34 @@ def block_shortest(mu, B, k, h):
     return best
 
 
-@pytest.mark.parametrize("inst", CASES, ids=lambda x: x.tag)
-@pytest.mark.parametrize("beta", [4, 10])
-def test_same_lattice_and_volume(inst, beta):
-    _, kern, _ = O.reduce(inst.A, inst.d)
-    r = O.bkz(kern, beta)
-    kb = r.kern.astype(np.int64)
+# Instances on which LLL leaves work for the block search: some block of
+# width 4 of the LLL basis is not delta-reduced, and its first vector is not
+# a shortest one (squared norms 24 against 20, and 73 against 25).  On the
+# small-D cases the LLL basis often passes these checks already and BKZ
+# inserts nothing, so only these show that the block search finds what is
+# missing and that its insertions keep the lattice.
+HARD = [I.small(2003, 2, 20, 200), I.small(2005, 3, 24, 1000)]
+
+
+def assert_same_lattice(kern, kb):
+    """kb = U kern with U integral and |det U| = 1, and equal Gram volumes."""
+    kb = kb.astype(np.int64)
     U = np.rint(kb.astype(float) @ np.linalg.pinv(kern.astype(float))).astype(np.int64)
     assert np.array_equal(U @ kern.astype(np.int64), kb)
     assert abs(bareiss_det(U)) == 1
     G0 = kern.astype(object) @ kern.astype(object).T
     G1 = kb.astype(object) @ kb.astype(object).T
     assert bareiss_det(G0) == bareiss_det(G1)
+
+
+@pytest.mark.parametrize("inst", CASES + HARD, ids=lambda x: x.tag)
+@pytest.mark.parametrize("beta", [4, 10])
+def test_same_lattice_and_volume(inst, beta):
+    _, kern, _ = O.reduce(inst.A, inst.d)
+    r = O.bkz(kern, beta)
+    if any(inst is h for h in HARD):
+        assert r.inserts > 0
+    assert_same_lattice(kern, r.kern)
 
 
 @pytest.mark.parametrize("inst", CASES[:4], ids=lambda x: x.tag)
@@ -129,14 +145,6 @@ def test_full_block_gives_a_shortest_vector():
     mu, B = exact_gso(kb)
     lam = block_shortest(mu, B, 0, dd)
     assert float(B[0]) <= float(lam) / 0.999999 * (1 + 1e-12)
-
-
-# Instances on which LLL leaves work for the block search: some block of
-# width 4 of the LLL basis is not delta-reduced, and its first vector is not
-# a shortest one (squared norms 24 against 20, and 73 against 25).  On the
-# small-D cases above the LLL basis often passes these checks already, so
-# only these show that the block search finds and inserts what is missing.
-HARD = [I.small(2003, 2, 20, 200), I.small(2005, 3, 24, 1000)]
 
 
 @pytest.mark.parametrize("inst", HARD, ids=lambda x: x.tag)
@@ -164,6 +172,7 @@ def test_full_block_finds_the_shortest_vector_lll_missed(inst):
     kb = O.bkz(kern, dd, delta=0.999999).kern
     # ||b_0||^2 is an integer and at most lam / 0.999999, so it equals lam
     assert int(np.dot(kb[0].astype(np.int64), kb[0].astype(np.int64))) == lam
+    assert_same_lattice(kern, kb)
 
 
 @pytest.mark.parametrize("inst", CASES, ids=lambda x: x.tag)
