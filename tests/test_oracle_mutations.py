@@ -73,6 +73,14 @@ MUTANTS = [
     ("leaf without the range check on v", "static int leaf_check(",
      "if (v[c] > rmax || v[c] < -rmax || (v[c] + rmax) % cc != 0) return 0;",
      "if ((v[c] + rmax) % cc != 0) return 0;"),
+    ("bhat rows adding the projections instead of subtracting them", "int oracle_gso(",
+     "acc = fma(-mu[(size_t)i * dd + j], bhat", "acc = fma(mu[(size_t)i * dd + j], bhat"),
+    ("subtree start rebuilding rho from its last level only", "int oracle_enumerate_bounds(",
+     "rho0 = fma(xx, B[t], rho0);", "rho0 = fma(xx, B[t], 0.0);"),
+    ("walk position of a prefix value off by one", "static long level_position(",
+     "if (u == target) return pos;", "if (u == target) return pos + 1;"),
+    ("BKZ insertion step dropping the Bezout term of the first row", "int oracle_bkz(",
+     "const i128 v1 = -(i128)tb * c0[c] + (i128)sa * c1[c];", "const i128 v1 = (i128)sa * c1[c];"),
     ("bounded leaf without the per-variable scale c_j", "static int leaf_check(",
      "const int64_t cc = 2 * (rmax / (e->r ? e->r[c] : 1));", "const int64_t cc = 2 * rmax;"),
 ]
@@ -141,6 +149,8 @@ def _pins():
         for inst in TC.CASES[:2]:
             for sym in (False, True):
                 TC.test_split_prefixes_and_their_norms_are_exact(inst, sym)
+        for k in (1, 3, 6):
+            TE.test_split_is_a_partition(TE.SMALL[1], k)
 
     def lds():
         import test_oracle_lds as TD
@@ -148,6 +158,8 @@ def _pins():
             for inst in TD.CASES[:3]:
                 TD.test_iterations_partition_the_solution_set(inst, rank)
             TD.test_first_solution_comes_at_the_least_discrepancy(rank)
+            for k, depth in ((1, 3), (2, 5), (4, 6)):
+                TD.test_split_iteration_is_a_partition(TD.CASES[1], k, depth, rank)
 
     def bkz():
         import test_oracle_bkz as TB
@@ -156,6 +168,7 @@ def _pins():
             TB.test_blocks_are_reduced(inst)
         TB.test_full_block_gives_a_shortest_vector()
         for inst in TB.HARD:
+            TB.test_same_lattice_and_volume(inst, 4)
             TB.test_block_search_repairs_what_lll_leaves(inst)
             TB.test_full_block_finds_the_shortest_vector_lll_missed(inst)
 
