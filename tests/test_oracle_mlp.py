@@ -4,6 +4,8 @@ The loss gradient is checked against central finite differences of the
 loss on the exact (unrounded) network -- a wrong sign, a dropped term or a
 transposed weight in the backward formulas fails here -- and the forward
 pass and the bfloat16 rounding against values worked out by hand."""
+import math
+
 import numpy as np
 import pytest
 
@@ -35,7 +37,13 @@ def test_gradient_matches_finite_differences(pos_weight):
     found = (rng.random(9) < 0.4).astype(np.float64)
     ln = rng.normal(3, 1, 9)
     _, g = R.loss_and_grad(theta, x, found, ln, pos_weight, round_bf16=False)
-    idx = rng.choice(R.MLP_PARAMS, size=80, replace=False)
+    # 12 indices from every parameter block (all of b3): a uniform sample
+    # of 80 out of 6792 would leave the 64-entry biases mostly unchecked
+    idx, o = [], 0
+    for _, shape in R.SHAPES:
+        size = int(np.prod(shape))
+        idx.extend((o + rng.choice(size, size=min(12, size), replace=False)).tolist())
+        o += size
     h = 1e-6
     for i in idx:
         tp, tm = theta.copy(), theta.copy()
@@ -58,16 +66,8 @@ def test_forward_by_hand(round_bf16):
                y3 = 1 * 0 = 0, y7 = b3[7] = -0.125
     A missing ReLU (y2 = -48 or y3 = 2.75), a transposed layer or a dropped
     bias changes y."""
-    p = R.unpack(np.zeros(R.MLP_PARAMS))
-    p["W1"][0, 0], p["W1"][1, 1] = 2.0, -1.0
-    p["b1"][0], p["b1"][1] = 0.5, 0.25
-    p["W2"][0, 0], p["W2"][0, 1], p["W2"][1, 3] = 1.0, -2.0, -1.0
-    p["b2"][1], p["b2"][2] = 1.0, 0.75
-    p["W3"][0, 0], p["W3"][2, 1], p["W3"][1, 2], p["W3"][3, 3] = 2.0, 4.0, 8.0, 1.0
-    p["b3"][0], p["b3"][1], p["b3"][7] = -1.0, 0.5, -0.125
-    x = np.zeros((2, 32))
-    x[0, 0], x[0, 1] = 1.5, 3.0
-    y, _ = R.forward(R.pack(p), x, round_bf16=round_bf16)
+    theta, x = _hand_network()
+    y, _ = R.forward(theta, x, round_bf16=round_bf16)
     want = np.zeros((2, 8))
     want[0, :3] = [6.0, 3.5, 0.0]
     want[:, 7] = -0.125
@@ -79,6 +79,32 @@ def test_forward_by_hand(round_bf16):
     want[1, 1] = 4 * h2[2] + 0.5
     want[1, 2] = 8 * max(h2[1], 0.0)
     assert np.array_equal(y, want)
+
+
+def _hand_network():
+    """The network of test_forward_by_hand."""
+    p = R.unpack(np.zeros(R.MLP_PARAMS))
+    p["W1"][0, 0], p["W1"][1, 1] = 2.0, -1.0
+    p["b1"][0], p["b1"][1] = 0.5, 0.25
+    p["W2"][0, 0], p["W2"][0, 1], p["W2"][1, 3] = 1.0, -2.0, -1.0
+    p["b2"][1], p["b2"][2] = 1.0, 0.75
+    p["W3"][0, 0], p["W3"][2, 1], p["W3"][1, 2], p["W3"][3, 3] = 2.0, 4.0, 8.0, 1.0
+    p["b3"][0], p["b3"][1], p["b3"][7] = -1.0, 0.5, -0.125
+    x = np.zeros((2, 32))
+    x[0, 0], x[0, 1] = 1.5, 3.0
+    return R.pack(p), x
+
+
+def test_loss_by_hand():
+    """The loss of the documented contract on the network above (outputs
+    y = (6, 3.5) and (0, 3.5)): per row pos_weight * BCE(y0, found) for
+    found rows, BCE otherwise, plus 0.1 (y1 - log(1 + nodes))^2, averaged.
+      row 0: found, pos_weight 2: 2 log(1 + e^-6) + 0.1 (3.5 - 3.5)^2
+      row 1: not found:           log 2           + 0.1 (3.5 - 1.5)^2 = log 2 + 0.4"""
+    theta, x = _hand_network()
+    loss, _ = R.loss_and_grad(theta, x, np.array([1.0, 0.0]), np.array([3.5, 1.5]), pos_weight=2.0)
+    want = (2 * math.log1p(math.exp(-6.0)) + math.log(2.0) + 0.4) / 2
+    assert loss == pytest.approx(want, rel=1e-12)
 
 
 def test_score_ranks_by_solution_probability():
