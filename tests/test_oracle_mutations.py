@@ -253,3 +253,82 @@ def test_the_unmodified_oracle_passes_every_pin(outcomes):
 def test_each_planted_mistake_fails_a_pin(outcomes, name):
     res = outcomes[name]
     assert any(v != "pass" for v in res.values()), res
+
+
+# --------------------------------------------------------------------------
+# The scorer's CPU reference (oracle/mlp.py): planted mistakes in copies of
+# the module, each loaded in place of the original for the scorer's pins.
+
+MLP_SRC = os.path.join(ROOT, "oracle", "mlp.py")
+
+MLP_MUTANTS = [
+    ("BCE gradient of the wrong sign",
+     "(1.0 / (1.0 + np.exp(-z)) - f)", "(f - 1.0 / (1.0 + np.exp(-z)))"),
+    ("node-term gradient without the factor 2",
+     "dy[:, 1] = 2.0 * NODE_WEIGHT * diff / B", "dy[:, 1] = NODE_WEIGHT * diff / B"),
+    ("backward without the second ReLU's mask",
+     "dh2 = (dyr @ r(p[\"W3\"]).T) * (c[\"a2\"] > 0)", "dh2 = (dyr @ r(p[\"W3\"]).T)"),
+    ("W2 gradient transposed",
+     "g[\"W2\"] = c[\"h1b\"].T @ dh2r", "g[\"W2\"] = (c[\"h1b\"].T @ dh2r).T"),
+    ("b1 gradient taken from the second layer",
+     "g[\"b1\"] = dh1.sum(axis=0)", "g[\"b1\"] = dh2.sum(axis=0)"),
+    ("pos_weight on the rows without a solution",
+     "np.where(f > 0.5, pos_weight, 1.0)", "np.where(f > 0.5, 1.0, pos_weight)"),
+    ("bfloat16 rounding with ties away from zero",
+     "r = ((u + 0x7FFF + lsb) >> 16) << 16", "r = ((u + 0x8000) >> 16) << 16"),
+    ("forward without the second bias",
+     "a2 = h1b @ r(p[\"W2\"]) + p[\"b2\"]", "a2 = h1b @ r(p[\"W2\"])"),
+    ("node term weighted 0.2 (loss and gradient alike)",
+     "NODE_WEIGHT = 0.1", "NODE_WEIGHT = 0.2"),
+]
+
+
+def _mlp_pins_fail(module):
+    """Names of the scorer pins that fail with `module` in place of oracle.mlp."""
+    import test_oracle_mlp as TM
+    saved = TM.R
+    TM.R = module
+    failed = []
+    try:
+        checks = {"bf16": lambda: TM.test_bf16_rounding_by_hand(),
+                  "layout": lambda: TM.test_param_count_and_layout(),
+                  "finite differences": lambda: [TM.test_gradient_matches_finite_differences(w) for w in (1.0, 7.5)],
+                  "forward": lambda: [TM.test_forward_by_hand(rb) for rb in (False, True)],
+                  "loss": lambda: TM.test_loss_by_hand()}
+        for name, fn in checks.items():
+            try:
+                fn()
+            except (KeyboardInterrupt, SystemExit):
+                raise
+            except BaseException:
+                failed.append(name)
+    finally:
+        TM.R = saved
+    return failed
+
+
+def _load_mlp(text, path):
+    import importlib.util
+    with open(path, "w") as f:
+        f.write(text)
+    spec = importlib.util.spec_from_file_location(os.path.splitext(os.path.basename(path))[0], path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_mlp_mutations_apply_once():
+    src = open(MLP_SRC).read()
+    for name, old, new in MLP_MUTANTS:
+        assert src.count(old) == 1, name
+
+
+def test_unmodified_scorer_reference_passes_its_pins(tmp_path):
+    assert _mlp_pins_fail(_load_mlp(open(MLP_SRC).read(), str(tmp_path / "mlp_copy.py"))) == []
+
+
+@pytest.mark.parametrize("k", range(len(MLP_MUTANTS)), ids=[m[0] for m in MLP_MUTANTS])
+def test_each_planted_scorer_mistake_fails_a_pin(tmp_path, k):
+    name, old, new = MLP_MUTANTS[k]
+    mod = _load_mlp(open(MLP_SRC).read().replace(old, new), str(tmp_path / f"mlp_mutant{k}.py"))
+    assert _mlp_pins_fail(mod), name
