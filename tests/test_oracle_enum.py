@@ -130,6 +130,21 @@ def test_first_mode_returns_a_valid_solution():
     assert np.array_equal(inst.A.astype(np.int64) @ x, inst.d)
 
 
+@pytest.mark.parametrize("k", [0, 1, 2], ids=lambda k: SMALL[k].tag)
+def test_first_mode_stops_at_one_of_many(k):
+    """First-solution mode (Sec. 1: any solution answers fMSP) on instances
+    with 107-451 solutions: exactly one is reported, it is in the
+    brute-force set, and the walk stops early."""
+    inst = SMALL[k]
+    want = DEF.brute_force(inst.A, inst.d)
+    assert len(want) > 100
+    full = O.solve(inst.A, inst.d).result
+    r = O.solve(inst.A, inst.d, first=True).result
+    assert r.stopped and r.nsol == 1
+    assert any(np.array_equal(r.solutions[0], w) for w in want)
+    assert r.nodes < full.nodes
+
+
 def test_infeasible_instance_has_no_solution():
     """Cornuejols-Dawande right-hand side d_i = floor(sum_j a_ij / 2) with a
     parity twist that makes it infeasible: d odd where every a_ij is even."""
