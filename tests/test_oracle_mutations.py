@@ -81,6 +81,14 @@ MUTANTS = [
      "if (u == target) return pos;", "if (u == target) return pos + 1;"),
     ("BKZ insertion step dropping the Bezout term of the first row", "int oracle_bkz(",
      "const i128 v1 = -(i128)tb * c0[c] + (i128)sa * c1[c];", "const i128 v1 = (i128)sa * c1[c];"),
+    ("filter-only Hoelder mode cutting like the default", "static void enum_level(",
+     "if (fail && e->o.hoelder == HOELDER_CUT) {", "if (fail && e->o.hoelder != HOELDER_OFF) {"),
+    ("Hoelder failure still expanded", "static void enum_level(",
+     "if (!fail) {", "if (1) {"),
+    ("first-solution mode whose stop does not reach the levels above", "static void enum_level(",
+     "if (e->s.stopped) return;", "if (0) return;"),
+    ("literal mode normalising the sign at the leaf", "static int leaf_check(",
+     "    if (e->o.sym) {", "    if (1) {"),
     ("bounded leaf without the per-variable scale c_j", "static int leaf_check(",
      "const int64_t cc = 2 * (rmax / (e->r ? e->r[c] : 1));", "const int64_t cc = 2 * rmax;"),
 ]
@@ -151,6 +159,9 @@ def _pins():
                 TC.test_split_prefixes_and_their_norms_are_exact(inst, sym)
         for k in (1, 3, 6):
             TE.test_split_is_a_partition(TE.SMALL[1], k)
+        TE.test_first_mode_returns_a_valid_solution()
+        for k in (0, 1, 2):
+            TE.test_first_mode_stops_at_one_of_many(k)
 
     def lds():
         import test_oracle_lds as TD
