@@ -89,6 +89,13 @@ MUTANTS = [
      "if (e->s.stopped) return;", "if (0) return;"),
     ("literal mode normalising the sign at the leaf", "static int leaf_check(",
      "    if (e->o.sym) {", "    if (1) {"),
+    ("reduction's mu scaled by the row's own reciprocal", "static void gso_row(",
+     "mu[(size_t)k * K + j] = acc * invB[j];", "mu[(size_t)k * K + j] = acc * invB[k];"),
+    ("LLL swap leaving the Gram matrix's columns in place", "static int lll_core(",
+     "for (int i = 0; i < K; ++i) {      /* swap columns k-1, k of G */",
+     "for (int i = 0; i < 0; ++i) {      /* swap columns k-1, k of G */"),
+    ("Lovasz test reading mu of the row above", "static int lll_core(",
+     "double mk = mu[(size_t)k * K + (k - 1)];", "double mk = mu[(size_t)(k - 1) * K + (k > 1 ? k - 2 : 0)];"),
     ("bounded leaf without the per-variable scale c_j", "static int leaf_check(",
      "const int64_t cc = 2 * (rmax / (e->r ? e->r[c] : 1));", "const int64_t cc = 2 * rmax;"),
 ]
