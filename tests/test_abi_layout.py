@@ -159,3 +159,27 @@ def test_binding_signatures_follow_the_header():
             assert fn.restype is None, name
         else:
             assert _matches(ret, fn.restype), (name, ret, fn.restype)
+
+
+def test_header_compiles_as_c_and_cpp(tmp_path):
+    """include/msp.h stands alone in C99 and in C++11 (its extern "C" block
+    gives the C++ declarations C linkage)."""
+    import shutil
+    for compiler, std, ext in (("gcc", "-std=c99", "c"), ("g++", "-std=c++11", "cpp")):
+        cc = shutil.which(compiler)
+        if not cc:
+            pytest.skip(f"no {compiler}")
+        src = tmp_path / f"use.{ext}"
+        src.write_text('#include "msp.h"\nint main(void) { msp_opts o; (void)o; return 0; }\n')
+        subprocess.run([cc, std, "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                        "-c", str(src), "-o", str(tmp_path / f"use_{ext}.o")], check=True)
+    # the C++ compile sees C linkage: no mangled msp_ names in an object that calls one
+    src = tmp_path / "call.cpp"
+    src.write_text('#include "msp.h"\nint f() { return msp_mlp_param_count(); }\n')
+    obj = tmp_path / "call.o"
+    subprocess.run([shutil.which("g++"), "-std=c++11", "-I", os.path.join(ROOT, "include"), "-c", str(src),
+                    "-o", str(obj)], check=True)
+    nm = shutil.which("nm")
+    if nm:
+        syms = subprocess.run([nm, str(obj)], check=True, capture_output=True, text=True).stdout
+        assert " msp_mlp_param_count" in syms and "_Z19msp_mlp_param_countv" not in syms
