@@ -325,7 +325,7 @@ def _mlp_pins_fail(module):
     return failed
 
 
-def _load_mlp(text, path):
+def _load_module(text, path):
     import importlib.util
     with open(path, "w") as f:
         f.write(text)
@@ -342,11 +342,74 @@ def test_mlp_mutations_apply_once():
 
 
 def test_unmodified_scorer_reference_passes_its_pins(tmp_path):
-    assert _mlp_pins_fail(_load_mlp(open(MLP_SRC).read(), str(tmp_path / "mlp_copy.py"))) == []
+    assert _mlp_pins_fail(_load_module(open(MLP_SRC).read(), str(tmp_path / "mlp_copy.py"))) == []
 
 
 @pytest.mark.parametrize("k", range(len(MLP_MUTANTS)), ids=[m[0] for m in MLP_MUTANTS])
 def test_each_planted_scorer_mistake_fails_a_pin(tmp_path, k):
     name, old, new = MLP_MUTANTS[k]
-    mod = _load_mlp(open(MLP_SRC).read().replace(old, new), str(tmp_path / f"mlp_mutant{k}.py"))
+    mod = _load_module(open(MLP_SRC).read().replace(old, new), str(tmp_path / f"mlp_mutant{k}.py"))
     assert _mlp_pins_fail(mod), name
+
+
+# --------------------------------------------------------------------------
+# The solution set's plain definitions (oracle/definition.py): planted
+# mistakes in copies of the module, each loaded in place of the original for
+# the pins that use the definitions.
+
+DEF_SRC = os.path.join(ROOT, "oracle", "definition.py")
+
+DEF_MUTANTS = [
+    ("binary vectors with the bit index off by one",
+     "((idx[:, None] >> np.arange(k, dtype=np.int64)) & 1)",
+     "((idx[:, None] >> (np.arange(k, dtype=np.int64) + 1)) & 1)"),
+    ("meet in the middle joining A x2 + d instead of d - A x2",
+     "S2 = d[None, :] - X2.astype(np.int64) @ A[:, h:].T",
+     "S2 = d[None, :] + X2.astype(np.int64) @ A[:, h:].T"),
+    ("solutions sorted by the last column first",
+     "keys = [x[:, c] for c in range(n - 1, -1, -1)]", "keys = [x[:, c] for c in range(n)]"),
+    ("box brute force without the upper bound",
+     "    radix = r + 1\n", "    radix = r\n"),
+]
+
+
+def _def_pins_fail(module):
+    """Names of the pins that fail with `module` in place of oracle.definition."""
+    import test_oracle_bounds as TN
+    import test_oracle_enum as TE
+    saved = (TE.DEF, TN.DEF)
+    TE.DEF = TN.DEF = module
+    failed = []
+    try:
+        checks = {"hand example": lambda: TE.test_definition_hand_example(),
+                  "methods agree": lambda: [TE.test_definition_methods_agree(s) for s in range(4)],
+                  "enumeration": lambda: [TE.test_all_modes_equal_brute_force(TE.SMALL[k]) for k in range(3)],
+                  "bounds": lambda: [TN.test_bounded_solution_sets_equal_brute_force(TN.CASES[k], 0, True)
+                                     for k in range(3)]}
+        for name, fn in checks.items():
+            try:
+                fn()
+            except (KeyboardInterrupt, SystemExit):
+                raise
+            except BaseException:
+                failed.append(name)
+    finally:
+        TE.DEF, TN.DEF = saved
+    return failed
+
+
+def test_definition_mutations_apply_once():
+    src = open(DEF_SRC).read()
+    for name, old, new in DEF_MUTANTS:
+        assert src.count(old) == 1, name
+
+
+def test_unmodified_definitions_pass_their_pins(tmp_path):
+    assert _def_pins_fail(_load_module(open(DEF_SRC).read(), str(tmp_path / "definition_copy.py"))) == []
+
+
+@pytest.mark.parametrize("k", range(len(DEF_MUTANTS)), ids=[m[0] for m in DEF_MUTANTS])
+def test_each_planted_definition_mistake_fails_a_pin(tmp_path, k):
+    name, old, new = DEF_MUTANTS[k]
+    mod = _load_module(open(DEF_SRC).read().replace(old, new), str(tmp_path / f"definition_mutant{k}.py"))
+    assert _def_pins_fail(mod), name
